@@ -1,0 +1,440 @@
+"""Benchmark of the parametric GEMM hot path on GB300.
+
+One step = one GEMM C = A*B at M = N = K = 8192 (FP32 inputs, FP32 output) in
+the chosen arithmetic form, with every stage of the path inside the step:
+operand preparation (for the tensor-core forms) and the GEMM kernel; the case
+discussion runs on the host before each launch.  Inputs (256 MiB each) exceed
+the 129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `value` is whole-job TFLOP/s (2 M N K per GEMM,
+all ranks), `roofline` describes the dominant kernel (the GEMM), `cpu_baseline`
+the FP64 CPU oracle on a bounded sample of rows of the same product.
+
+--impl reference times the oracle itself (the CPU reference arm) on the same
+workload, a bounded sample of rows per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+MEASURED_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                     "sm_max_mhz": 2070.0}
+METRIC = "GEMM TFLOP/s & % roofline, chosen form vs plain FP32 tuned, at stated rel. error"
+FORM_NAMES = {"f32": "FP32 SIMT (register-blocked parametric kernel)",
+              "split": "split-BF16 (3 BF16 products, tcgen05, FP32 accumulate)",
+              "bf16": "BF16 tcgen05, FP32 accumulate",
+              "fp8": "FP8-E4M3 per-128x128-tile scaled tcgen05, FP32 accumulate"}
+FORM_DTYPE = {"f32": "f32", "split": "bf16", "bf16": "bf16", "fp8": "fp8-e4m3"}
+FORM_TOL = {"f32": 1e-5, "split": 2e-5, "bf16": 2e-2, "fp8": 5e-2}
+
+
+def peaks():
+    p = dict(MEASURED_FALLBACK)
+    src = "fallback"
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p.update(json.load(f))
+        src = "measured"
+    return p, src
+
+
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(M, N, K, seed, target_s=12.0):
+    """Time the FP64 oracle on a bounded sample of full output rows."""
+    import numpy as np
+
+    import oracle
+    from paper_1801_04348_gb300 import inputs
+    A, B = inputs.gemm_operands(M, N, K, seed=seed)
+    oracle.build()
+    rows = np.arange(2, dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.gemm(A, B, rows=rows)
+    t1 = time.perf_counter() - t0
+    cores = oracle.max_threads()
+    nrows = int(max(cores, min(M, round(target_s / max(t1 / 2, 1e-6)))))
+    nrows = max(cores, (nrows // cores) * cores)
+    rows = np.linspace(0, M - 1, nrows).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.gemm(A, B, rows=rows)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * nrows * N * K
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nrows} of {M} output rows of the {M}x{N}x{K} product in FP64 "
+                      f"(i-k-j loop, OpenMP), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1801_04348_gb300 import inputs
+    M = N = K = args.size
+    A, B = inputs.gemm_operands(M, N, K, seed=0)
+    oracle.build()
+    cores = oracle.max_threads()
+    # bounded sample per step so that the whole run stays within a few minutes
+    per_step_rows = max(cores, 2 * cores)
+    rows_all = np.linspace(0, M - 1, per_step_rows * (args.steps + args.warmup)).astype(np.int64)
+    for w in range(args.warmup):
+        oracle.gemm(A, B, rows=rows_all[w * per_step_rows:(w + 1) * per_step_rows])
+    times = []
+    for s in range(args.steps):
+        r = rows_all[(args.warmup + s) * per_step_rows:(args.warmup + s + 1) * per_step_rows]
+        t0 = time.perf_counter()
+        oracle.gemm(A, B, rows=r)
+        times.append(time.perf_counter() - t0)
+    flops = 2.0 * per_step_rows * N * K
+    tot = sum(times)
+    value = flops * len(times) / tot / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{M}x{N}x{K} FP32-input GEMM, FP64 CPU oracle, "
+                                   f"{per_step_rows} sampled output rows per step",
+                       "M": M, "N": N, "K": K},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step_rows} of {M} output rows per step"},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="auto", choices=["auto", "f32", "split", "bf16", "fp8"])
+    ap.add_argument("--size", type=int, default=8192)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_1801_04348_gb300 import build as pbuild
+    from paper_1801_04348_gb300 import inputs, pgk
+
+    ws, rank, local = dist_env()
+    pbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    M = N = K = args.size
+    A, B = inputs.gemm_operands(M, N, K, seed=rank)
+    Ad = torch.from_numpy(A).to(dev)
+    Bd = torch.from_numpy(B).to(dev)
+    C = torch.empty(M, N, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    machine = pgk.machine_query(local)
+
+    forms = [args.form] if args.form != "auto" else ["split", "f32"]
+    form, prog, err = None, None, None
+    for f in forms:
+        try:
+            prog, err = prepare_form(f, Ad, Bd, C, A, B, stream, pgk, torch, np)
+            if err <= FORM_TOL[f]:
+                form = f
+                break
+        except pgk.PgkError:
+            continue
+    if form is None:
+        raise SystemExit("no arithmetic form met its tolerance")
+
+    step, gemm_events, launches_per_step, alg = make_step(form, prog, Ad, Bd, C, M, N, K, sh, pgk,
+                                                          torch, dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    gemm_ms = [a.elapsed_time(b) for a, b in gemm_events[-args.steps:]] if gemm_events else []
+    t_local = ms / 1e3
+    if ws > 1:
+        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    flops = 2.0 * M * N * K * args.steps * ws
+    value = flops / t_max / 1e12
+
+    # end to end: host (pinned) inputs -> device -> GEMM -> host result
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(form, prog, A, B, M, N, K, dev, stream, pgk, torch, args, ws)
+
+    pk, pk_src = peaks()
+    roof = roofline(form, alg, gemm_ms, ms / args.steps, machine, pk, pk_src, clocks)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(M, N, K, seed=0)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC,
+        "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPE[form], "data": "synthetic",
+        "config": {"workload": f"{M}x{N}x{K} GEMM, FP32 in/out, uniform[-1,1] seed 0(+rank), "
+                               f"form: {FORM_NAMES[form]}",
+                   "M": M, "N": N, "K": K, "form": form, "program_params": list(prog.as_tuple()),
+                   "rel_frobenius_err": err, "tolerance": FORM_TOL[form],
+                   "l2": "inputs 256 MiB each > 129 MB L2; no flush"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def prepare_form(form, Ad, Bd, C, A, B, stream, pgk, torch, np):
+    """Autotune the form's program parameters on the real operands and measure
+    its relative Frobenius error on 64 sampled rows against the FP64 oracle."""
+    import oracle
+    dt = {"f32": pgk.F32, "split": pgk.SPLIT_BF16, "bf16": pgk.BF16, "fp8": pgk.FP8_E4M3}[form]
+    with torch.cuda.stream(stream):
+        if form == "f32":
+            cands = [p for p in pgk.default_candidates(dt) if p.sr > 1]
+        else:
+            cands = pgk.default_candidates(dt)
+        best, _ = pgk.autotune(Ad, Bd, C, dt, candidates=cands, reps=2, stream=stream)
+        pgk.gemm(Ad, Bd, C, dt, best, stream=stream)
+    torch.cuda.synchronize()
+    M = A.shape[0]
+    rows = np.linspace(0, M - 1, 64).astype(np.int64)
+    ref = oracle.gemm(A, B, rows=rows)
+    got = C[torch.from_numpy(rows).to(C.device)].cpu().numpy()
+    return best, oracle.rel_frobenius(got, ref)
+
+
+def make_step(form, prog, Ad, Bd, C, M, N, K, sh, pgk, torch, dev):
+    """Returns (step callable, list of (start, end) events around the GEMM
+    kernel, kernel launches per step, algorithmic work per GEMM launch)."""
+    events = []
+    if form == "f32":
+        def step():
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            pgk.gemm(Ad, Bd, C, pgk.F32, prog, stream=sh)
+            b.record()
+            events.append((a, b))
+        return step, events, 1, {"flops": 2.0 * M * N * K}
+    Kp = (K + 15) // 16 * 16
+    if form == "split":
+        Ah = torch.empty(M, Kp, dtype=torch.int16, device=dev)
+        Al = torch.empty_like(Ah)
+        Bh = torch.empty(N, Kp, dtype=torch.int16, device=dev)
+        Bl = torch.empty_like(Bh)
+
+        def step():
+            pgk.split_bf16(Ad, Ah, Al, 0, stream=sh)
+            pgk.split_bf16(Bd, Bh, Bl, 1, stream=sh)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            pgk.gemm_lowp(M, N, K, pgk.SPLIT_BF16, Ah, Kp, Bh, Kp, C, N, A_lo=Al, Bt_lo=Bl,
+                          prog=prog, stream=sh)
+            b.record()
+            events.append((a, b))
+        return step, events, 3, {"flops": 6.0 * M * N * K}
+    if form == "bf16":
+        Ah = torch.empty(M, Kp, dtype=torch.int16, device=dev)
+        Bh = torch.empty(N, Kp, dtype=torch.int16, device=dev)
+
+        def step():
+            pgk.cvt_bf16(Ad, Ah, 0, stream=sh)
+            pgk.cvt_bf16(Bd, Bh, 1, stream=sh)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            pgk.gemm_lowp(M, N, K, pgk.BF16, Ah, Kp, Bh, Kp, C, N, prog=prog, stream=sh)
+            b.record()
+            events.append((a, b))
+        return step, events, 3, {"flops": 2.0 * M * N * K}
+    Aq = torch.empty(M, Kp, dtype=torch.uint8, device=dev)
+    Bq = torch.empty(N, Kp, dtype=torch.uint8, device=dev)
+    sA = torch.empty((M + 127) // 128, (K + 127) // 128, device=dev)
+    sB = torch.empty((K + 127) // 128, (N + 127) // 128, device=dev)
+
+    def step():
+        pgk.quant_fp8(Ad, Aq, sA, 0, stream=sh)
+        pgk.quant_fp8(Bd, Bq, sB, 1, stream=sh)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        pgk.gemm_lowp(M, N, K, pgk.FP8_E4M3, Aq, Kp, Bq, Kp, C, N, scaleA=sA, scaleB=sB, prog=prog,
+                      stream=sh)
+        b.record()
+        events.append((a, b))
+    return step, events, 3, {"flops": 2.0 * M * N * K}
+
+
+def roofline(form, alg, gemm_ms, step_ms, machine, pk, pk_src, clocks):
+    kern_ms = statistics.mean(gemm_ms) if gemm_ms else step_ms
+    achieved = alg["flops"] / (kern_ms * 1e-3) / 1e12
+    if form == "f32":
+        f = pk.get("sm_max_mhz", 2070.0)
+        peak = machine.sm_count * 128 * 2 * f * 1e6 / 1e12
+        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "frac": achieved / peak, "traffic": None,
+               "kernel": "k_rb (register-blocked FP32 SIMT)",
+               "peak_source": f"{machine.sm_count} SMs x 128 FP32 lanes x 2 flop x {f:.0f} MHz "
+                              f"(max SM clock, {pk_src})"}
+        if clocks.get("sm_mhz"):
+            out["frac_at_observed_clock"] = achieved / (peak * clocks["sm_mhz"] / f)
+        return out
+    if form == "fp8":
+        peak = 2.0 * pk["bf16_tflops"]
+        src = f"2 x bf16 burst ({pk_src}); FP8 dense = 2x BF16 nominal"
+    else:
+        peak = pk["bf16_tflops"]
+        src = f"bf16 burst ({pk_src})"
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "k_tc_gemm (tcgen05)",
+            "peak_source": src, "flops_per_launch": alg["flops"]}
+
+
+def measure_e2e(form, prog, A, B, M, N, K, dev, stream, pgk, torch, args, ws):
+    """Same metric through pgk_gemm with host buffers: per step the pinned host
+    inputs are copied to the device, the GEMM runs, C is copied back."""
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    Ch = torch.empty(M, N, dtype=torch.float32).pin_memory()
+    Ad = torch.empty(M, K, device=dev)
+    Bd = torch.empty(K, N, device=dev)
+    Cd = torch.empty(M, N, device=dev)
+    dt = {"f32": pgk.F32, "split": pgk.SPLIT_BF16, "bf16": pgk.BF16, "fp8": pgk.FP8_E4M3}[form]
+    steps = max(3, min(args.steps, 5))
+
+    def step():
+        Ad.copy_(Ah, non_blocking=True)
+        Bd.copy_(Bh, non_blocking=True)
+        pgk.gemm(Ad, Bd, Cd, dt, prog, stream=stream.cuda_stream)
+        Ch.copy_(Cd, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        step()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": 2.0 * M * N * K * ws / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "h2d_bytes_per_step": (M * K + K * N) * 4, "d2h_bytes_per_step": M * N * 4,
+            "steps": steps, "ms_per_step": ms}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

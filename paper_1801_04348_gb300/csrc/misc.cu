@@ -1,0 +1,346 @@
+// Library workspaces, the device error word, the tuning cache and the
+// autotuner (the paper leaves program parameters to auto-tuning, Section 1).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pgk_internal.cuh"
+
+namespace pgk {
+
+pgk_params default_params(int M, int N, int K, pgk_dtype dtype);
+
+// -------------------------------------------------------------- workspaces
+static std::mutex g_ws_mu;
+static void* g_ws_ptr[WS_COUNT];
+static size_t g_ws_size[WS_COUNT];
+static unsigned int* g_err_word = nullptr;
+
+void* workspace(int slot, size_t bytes, pgk_status* st) {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    *st = PGK_OK;
+    if (slot < 0 || slot >= WS_COUNT) {
+        *st = PGK_ERR_INVALID_ARG;
+        return nullptr;
+    }
+    if (bytes == 0) bytes = 16;
+    if (g_ws_size[slot] < bytes) {
+        if (g_ws_ptr[slot]) {
+            cudaDeviceSynchronize();
+            cudaFree(g_ws_ptr[slot]);
+            g_ws_ptr[slot] = nullptr;
+            g_ws_size[slot] = 0;
+        }
+        // grow geometrically so that alternating sizes do not reallocate
+        size_t want = bytes + bytes / 4;
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("workspace allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+            *st = PGK_ERR_NO_MEMORY;
+            return nullptr;
+        }
+        g_ws_ptr[slot] = p;
+        g_ws_size[slot] = want;
+    }
+    return g_ws_ptr[slot];
+}
+
+unsigned int* device_error_word(pgk_status* st) {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    *st = PGK_OK;
+    if (!g_err_word) {
+        cudaError_t e = cudaMalloc(&g_err_word, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemset(g_err_word, 0, sizeof(unsigned int));
+        if (e != cudaSuccess) {
+            g_err_word = nullptr;
+            *st = cuda_fail(e, "error word allocation");
+            return nullptr;
+        }
+    }
+    return g_err_word;
+}
+
+void free_workspaces() {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    bool any = g_err_word != nullptr;
+    for (int i = 0; i < WS_COUNT; ++i) any = any || g_ws_ptr[i] != nullptr;
+    if (any) cudaDeviceSynchronize();
+    for (int i = 0; i < WS_COUNT; ++i) {
+        if (g_ws_ptr[i]) cudaFree(g_ws_ptr[i]);
+        g_ws_ptr[i] = nullptr;
+        g_ws_size[i] = 0;
+    }
+    if (g_err_word) cudaFree(g_err_word);
+    g_err_word = nullptr;
+}
+
+// ------------------------------------------------------------ tuning cache
+static std::mutex g_tc_mu;
+static std::map<std::string, pgk_params> g_tune;
+
+static std::string tune_key(int M, int N, int K, pgk_dtype dtype) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp p;
+    char name[300] = "unknown";
+    if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) {
+        snprintf(name, sizeof(name), "%s_sm%d%d", p.name, p.major, p.minor);
+    } else {
+        cudaGetLastError();
+    }
+    for (char* c = name; *c; ++c)
+        if (*c == ' ' || *c == '\t') *c = '_';
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s %d %d %d %d", name, M, N, K, (int)dtype);
+    return buf;
+}
+
+void tune_cache_release() {
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    g_tune.clear();
+}
+
+// -------------------------------------------------------- default candidates
+static int simt_candidates(pgk_params* out, int cap) {
+    // every compiled register-blocked variant plus the paper-form grid of the
+    // paper's experiment shapes (B0, B1 in {8,16,32}, s in {1,2,4}, BK = B0)
+    std::vector<pgk_params> c;
+    std::vector<Variant>& r = registry();
+    for (size_t i = 0; i < r.size(); ++i) {
+        const pgk_variant_info& v = r[i].info;
+        if (v.family != PGK_FAM_RB) continue;
+        pgk_params p = {v.B0, v.B1, v.s, v.sr, v.tile};
+        c.push_back(p);
+    }
+    const int bs[3] = {8, 16, 32}, ss[3] = {1, 2, 4};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int s = 0; s < 3; ++s) {
+                if (bs[a] > bs[b] * ss[s]) continue;
+                pgk_params p = {bs[a], bs[b], ss[s], 1, 0};
+                c.push_back(p);
+            }
+    const int n = (int)c.size();
+    for (int i = 0; i < n && i < cap && out; ++i) out[i] = c[i];
+    return n;
+}
+
+static int tc_candidates(pgk_dtype dtype, pgk_params* out, int cap) {
+    std::vector<pgk_params> c;
+    if (dtype == PGK_SPLIT_BF16) {
+        pgk_params a = {128, 128, 3, 0, 0}, b = {128, 256, 2, 0, 0};
+        c.push_back(a);
+        c.push_back(b);
+    } else if (dtype == PGK_BF16) {
+        pgk_params a = {128, 256, 4, 0, 0}, b = {128, 128, 6, 0, 0};
+        c.push_back(a);
+        c.push_back(b);
+    } else {
+        pgk_params a = {128, 128, 4, 0, 0}, b = {128, 256, 3, 0, 0};
+        c.push_back(a);
+        c.push_back(b);
+    }
+    const int n = (int)c.size();
+    for (int i = 0; i < n && i < cap && out; ++i) out[i] = c[i];
+    return n;
+}
+
+}  // namespace pgk
+
+using namespace pgk;
+
+extern "C" {
+
+pgk_status pgk_tune_cache_put(int M, int N, int K, pgk_dtype dtype, const pgk_params* p) {
+    if (!p) {
+        set_error("NULL params");
+        return PGK_ERR_INVALID_ARG;
+    }
+    const std::string k = tune_key(M, N, K, dtype);
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    g_tune[k] = *p;
+    return PGK_OK;
+}
+
+pgk_status pgk_tune_cache_get(int M, int N, int K, pgk_dtype dtype, pgk_params* p) {
+    if (!p) {
+        set_error("NULL params");
+        return PGK_ERR_INVALID_ARG;
+    }
+    const std::string k = tune_key(M, N, K, dtype);
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    std::map<std::string, pgk_params>::iterator it = g_tune.find(k);
+    if (it == g_tune.end()) return PGK_ERR_INVALID_ARG;
+    *p = it->second;
+    return PGK_OK;
+}
+
+pgk_status pgk_tune_cache_save(const char* path) {
+    if (!path) {
+        set_error("NULL path");
+        return PGK_ERR_INVALID_ARG;
+    }
+    FILE* f = fopen(path, "w");
+    if (!f) {
+        set_error("cannot open %s for writing", path);
+        return PGK_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    fprintf(f, "# pgk tuning cache v1: device M N K dtype B0 B1 s sr tile\n");
+    for (std::map<std::string, pgk_params>::iterator it = g_tune.begin(); it != g_tune.end(); ++it)
+        fprintf(f, "%s %d %d %d %d %d\n", it->first.c_str(), it->second.B0, it->second.B1,
+                it->second.s, it->second.sr, it->second.tile);
+    fclose(f);
+    return PGK_OK;
+}
+
+pgk_status pgk_tune_cache_load(const char* path) {
+    if (!path) {
+        set_error("NULL path");
+        return PGK_ERR_INVALID_ARG;
+    }
+    FILE* f = fopen(path, "r");
+    if (!f) {
+        set_error("cannot open %s", path);
+        return PGK_ERR_INVALID_ARG;
+    }
+    char line[1024];
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    while (fgets(line, sizeof(line), f)) {
+        if (line[0] == '#') continue;
+        char dev[512];
+        int M, N, K, dt;
+        pgk_params p;
+        if (sscanf(line, "%511s %d %d %d %d %d %d %d %d %d", dev, &M, &N, &K, &dt, &p.B0, &p.B1,
+                   &p.s, &p.sr, &p.tile) == 10) {
+            char key[800];
+            snprintf(key, sizeof(key), "%s %d %d %d %d", dev, M, N, K, dt);
+            g_tune[key] = p;
+        }
+    }
+    fclose(f);
+    return PGK_OK;
+}
+
+int pgk_default_candidates(pgk_dtype dtype, pgk_params* out, int cap) {
+    if (dtype == PGK_F32) return simt_candidates(out, cap);
+    if (dtype == PGK_BF16 || dtype == PGK_SPLIT_BF16 || dtype == PGK_FP8_E4M3)
+        return tc_candidates(dtype, out, cap);
+    return 0;
+}
+
+pgk_status pgk_autotune(int M, int N, int K, pgk_dtype dtype, const float* A, int lda,
+                        const float* B, int ldb, float* C, int ldc, const pgk_params* candidates,
+                        int ncand, int reps, float* ms_out, pgk_params* best, const char* log_path,
+                        void* stream) {
+    if (!A || !B || !C || reps < 1 || (candidates && ncand < 1)) {
+        set_error("bad autotune arguments");
+        return PGK_ERR_INVALID_ARG;
+    }
+    std::vector<pgk_params> cand;
+    if (candidates) {
+        cand.assign(candidates, candidates + ncand);
+    } else {
+        const int n = pgk_default_candidates(dtype, NULL, 0);
+        cand.resize(n);
+        pgk_default_candidates(dtype, cand.data(), n);
+    }
+    pgk_machine m;
+    pgk_status st = current_machine(&m, NULL);
+    if (st != PGK_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    PGK_CUDA_TRY(cudaEventCreate(&e0), "cudaEventCreate");
+    PGK_CUDA_TRY(cudaEventCreate(&e1), "cudaEventCreate");
+    FILE* log = log_path ? fopen(log_path, "a") : NULL;
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    int best_i = -1;
+    float best_ms = INFINITY;
+    pgk_status last = PGK_OK;
+    for (size_t i = 0; i < cand.size(); ++i) {
+        float ms = INFINITY;
+        pgk_case c;
+        st = pgk_select_case(&m, M, N, K, dtype, &cand[i], &c);
+        if (st == PGK_OK) {
+            st = pgk_gemm(M, N, K, dtype, A, lda, B, ldb, C, ldc, 0, &cand[i], stream);  // warm-up
+            std::vector<float> t;
+            for (int r = 0; r < reps && st == PGK_OK; ++r) {
+                cudaEventRecord(e0, s);
+                st = pgk_gemm(M, N, K, dtype, A, lda, B, ldb, C, ldc, 0, &cand[i], stream);
+                cudaEventRecord(e1, s);
+                if (st != PGK_OK) break;
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "autotune timing");
+                    break;
+                }
+                float x = 0.f;
+                cudaEventElapsedTime(&x, e0, e1);
+                t.push_back(x);
+            }
+            if (st == PGK_OK && !t.empty()) {
+                std::sort(t.begin(), t.end());
+                ms = t[t.size() / 2];
+            }
+        }
+        if (st == PGK_ERR_CUDA) {
+            // a CUDA failure (e.g. out of resources) disqualifies the candidate;
+            // a sticky error would fail every later call, so stop there
+            cudaError_t sticky = cudaDeviceSynchronize();
+            if (sticky != cudaSuccess) {
+                last = cuda_fail(sticky, "autotune");
+                break;
+            }
+        }
+        if (ms_out) ms_out[i] = ms;
+        if (log) {
+            const double tflops = isfinite(ms) ? 2.0 * M * (double)N * K / (ms * 1e-3) / 1e12 : 0.0;
+            fprintf(log, "%s,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%.6f,%.4f\n", prop.name, M, N, K,
+                    (int)dtype, cand[i].B0, cand[i].B1, cand[i].s, cand[i].sr, cand[i].tile,
+                    st == PGK_OK ? c.leaf : -1, isfinite(ms) ? ms : -1.0, tflops);
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_i = (int)i;
+        }
+    }
+    if (log) fclose(log);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (last != PGK_OK) return last;
+    if (best_i < 0) {
+        set_error("no feasible candidate");
+        return PGK_ERR_INFEASIBLE;
+    }
+    if (best) *best = cand[best_i];
+    return pgk_tune_cache_put(M, N, K, dtype, &cand[best_i]);
+}
+
+pgk_status pgk_check_device_error(void) {
+    pgk_status st;
+    unsigned int* w = device_error_word(&st);
+    if (!w) return st;
+    unsigned int h = 0;
+    PGK_CUDA_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    PGK_CUDA_TRY(cudaMemcpy(&h, w, sizeof(h), cudaMemcpyDeviceToHost), "error word read");
+    if (h) {
+        unsigned int z = 0;
+        cudaMemcpy(w, &z, sizeof(z), cudaMemcpyHostToDevice);
+        set_error("a bounded device wait timed out (code 0x%x)", h);
+        return PGK_ERR_TIMEOUT;
+    }
+    return PGK_OK;
+}
+
+}  // extern "C"

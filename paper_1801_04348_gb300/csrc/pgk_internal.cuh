@@ -1,0 +1,90 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pgk.h"
+
+namespace pgk {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+void clear_error();
+// Converts a CUDA error into PGK_ERR_CUDA with a message naming `what`.
+pgk_status cuda_fail(cudaError_t e, const char* what);
+
+#define PGK_CUDA_TRY(call, what)                    \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return pgk::cuda_fail(e_, what); \
+    } while (0)
+
+// -------------------------------------------------------- SIMT arguments
+struct SimtArgs {
+    int M, N, K;
+    const float* A;
+    int lda;
+    const float* B;
+    int ldb;
+    float* C;
+    int ldc;
+    int beta;
+    int B0, B1, BK;        // runtime program parameters (paper/direct families)
+    int vecA, vecB, vecC;  // 16-byte vector access allowed on A / B / C rows
+};
+
+typedef cudaError_t (*simt_launch_fn)(const SimtArgs&, int smem_bytes, cudaStream_t);
+
+// One compiled variant of the registry.
+struct Variant {
+    pgk_variant_info info;      // regs / max_threads filled lazily
+    const void* func;           // __global__ function (for attributes)
+    simt_launch_fn launch;      // SIMT launcher (NULL for tensor-core variants)
+    int smem_fixed;             // dynamic shared memory of a fixed-shape variant
+};
+
+// Registration hooks, one per translation unit that defines variants.
+void register_simt_variants(std::vector<Variant>& v);
+void register_tc_variants(std::vector<Variant>& v);
+
+// Registry access (host.cu).
+std::vector<Variant>& registry();
+int find_paper_variant(int s, int regopt);
+int find_direct_variant(int regopt);
+int find_rb_variant(int B0, int B1, int sr, int s, int tile);
+// Register count of a variant on the current device (-1 if unavailable).
+int variant_regs(int id);
+
+// Shared-memory formulas (bytes) of the SIMT families: the f_smem evaluation.
+long long smem_paper(int B0, int B1, int s, int BK);
+long long smem_rb(int B0, int B1, int sr, int s, int BK);
+
+// ------------------------------------------------------------- workspace
+// Library-owned device memory, grown on demand, freed by pgk_shutdown().
+void* workspace(int slot, size_t bytes, pgk_status* st);
+enum { WS_A0 = 0, WS_A1, WS_B0, WS_B1, WS_SA, WS_SB, WS_TABLE, WS_COUNTER, WS_PARTIAL, WS_COUNT };
+// Device error word set by bounded waits (tensor-core kernels).
+unsigned int* device_error_word(pgk_status* st);
+void free_workspaces();
+
+// Machine parameters of the current device.
+pgk_status current_machine(pgk_machine* m, int* device);
+
+// ------------------------------------------------------- tensor-core path
+// Fills the tensor-core case for (dtype, prog) or returns an error.
+pgk_status tc_select(const pgk_machine* m, int M, int N, int K, pgk_dtype dtype,
+                     const pgk_params* prog, pgk_case* out);
+pgk_status tc_gemm_launch(const pgk_case& c, int M, int N, int K, pgk_dtype dtype,
+                          const void* A, int lda, const void* Bt, int ldbt, const void* A_lo,
+                          const void* Bt_lo, const float* sA, const float* sB, float* C, int ldc,
+                          int beta, cudaStream_t stream);
+
+// ------------------------------------------------------------- grouped
+void grouped_release();
+void tune_cache_release();
+
+}  // namespace pgk

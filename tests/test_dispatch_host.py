@@ -1,0 +1,103 @@
+"""The library's case walk (pgk_select_case_regs, host code) agrees at every
+point with the oracle's Algorithms 1-2 tree for the GEMM family, evaluated by
+brute force (each leaf's conjunction checked separately), on mock machines."""
+import numpy as np
+import pytest
+
+from oracle import comprehensive as co
+from oracle import dispatch
+from paper_1801_04348_gb300 import build as pbuild
+from paper_1801_04348_gb300 import pgk
+
+# register counts per class: paper s=1,2,4,8 ; capped ; direct ; direct capped ; rb
+TABLES = {
+    "small": [30, 34, 40, 56, 30, 32, 32, 40, 24, 24, 128],
+    "heavy": [70, 80, 90, 120, 60, 62, 63, 64, 80, 40, 168],
+}
+S_INDEX = {1: 0, 2: 1, 4: 2, 8: 3}
+
+
+def regs_fn(table):
+    def regs_of(prog):
+        fam, cap = prog["family"], prog["regopt"]
+        if fam == "direct":
+            return lambda e: 0 * e["B0"] + table[9 if cap else 8]
+        if fam == "rb":
+            return lambda e: 0 * e["B0"] + table[10]
+        if prog["s"] == "s":
+            def f(e):
+                out = np.zeros_like(e["s"])
+                for sv, si in S_INDEX.items():
+                    out = np.where(e["s"] == sv, table[si + (4 if cap else 0)], out)
+                return out
+            return f
+        return lambda e, s=prog["s"]: 0 * e["B0"] + table[S_INDEX[s] + (4 if cap else 0)]
+    return regs_of
+
+
+@pytest.fixture(scope="module")
+def built():
+    pbuild.build()
+    return pgk.lib()
+
+
+def _compare(box, family, table, rb_ok=lambda p: True):
+    leaves = dispatch.case_tree(family, regs_fn(table), box)
+    hits = dispatch.brute_force(leaves, box)
+    n = len(next(iter(box.values())))
+    checked = 0
+    for i in range(n):
+        pt = {k: int(v[i]) for k, v in box.items()}
+        if not rb_ok(pt):
+            continue
+        m = pgk.Machine(pt["T"], 49152, pt["ZB"], pt["RB"], 65536, pt["R"], 2048, 152, 32, 10, 3, 0)
+        prog = pgk.params(pt["B0"], pt["B1"], pt["s"], pt["sr"], pt["BK"])
+        st, c = pgk.select_case_regs(m, table, 64, 64, 64, pgk.F32, prog)
+        assert len(hits[i]) <= 1
+        if not hits[i]:
+            assert st == 2, (pt, st)                     # INFEASIBLE
+            continue
+        assert st == 0, (pt, st, pgk.last_error())
+        p, lam, _ = leaves[hits[i][0]]
+        assert c.leaf == dispatch.leaf_code(p), (pt, c.leaf, p)
+        assert c.regopt == int("1" in lam), (pt, lam)
+        want_fam = {"paper": pgk.FAM_PAPER, "rb": pgk.FAM_RB, "direct": pgk.FAM_DIRECT}[p["family"]]
+        assert c.family == want_fam
+        checked += 1
+    return checked
+
+
+@pytest.mark.parametrize("tname", list(TABLES))
+def test_paper_family_walk_matches_oracle(built, tname):
+    box = co.make_box({"T": [256, 1024], "R": [63, 255], "RB": [16384, 32768, 65536],
+                       "ZB": [0, 1024, 4096, 16384, 49152, 232448],
+                       "B0": [8, 16, 32], "B1": [8, 16, 32], "s": [1, 2, 4, 8], "sr": [1],
+                       "BK": [8, 16, 32]})
+    assert _compare(box, "paper", TABLES[tname]) > 100
+
+
+def test_rb_family_walk_matches_oracle(built):
+    compiled = set()
+    for i in range(pgk.num_variants()):
+        v = pgk.variant_info_get(i)
+        if v.family == pgk.FAM_RB:
+            compiled.add((v.B0, v.B1, v.sr, v.s, v.tile))
+    box = co.make_box({"T": [256, 1024], "R": [255], "RB": [32768, 65536],
+                       "ZB": [0, 4096, 16384, 65536, 232448],
+                       "B0": [8, 16, 32], "B1": [8, 16, 32], "s": [4, 8], "sr": [4, 8], "BK": [8, 16]})
+    ok = lambda p: (p["B0"], p["B1"], p["sr"], p["s"], p["BK"]) in compiled
+    assert _compare(box, "rb", TABLES["small"], ok) > 20
+    assert _compare(box, "rb", TABLES["heavy"], ok) > 5
+
+
+def test_real_gb300_like_machine_picks_4a3a(built):
+    m = pgk.Machine(1024, 49152, 232448, 65536, 65536, 255, 2048, 152, 32, 10, 3, 0)
+    for b0 in (8, 16, 32):
+        for b1 in (8, 16, 32):
+            for s in (1, 2, 4):
+                st, c = pgk.select_case_regs(m, TABLES["small"], 256, 256, 256, pgk.F32,
+                                             pgk.params(b0, b1, s))
+                if b0 <= b1 * s:
+                    assert st == 0 and c.leaf == pgk.LEAF_4A3A and c.params.tile == b0
+                else:
+                    assert st == 2
