@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--size", type=int, default=8192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--params", default=None,
+                    help="B0,B1,s,sr,tile: use these program parameters instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -220,7 +222,8 @@ def main():
     form, prog, err = None, None, None
     for f in forms:
         try:
-            prog, err = prepare_form(f, Ad, Bd, C, A, B, stream, pgk, torch, np)
+            fixed = pgk.params(*[int(x) for x in args.params.split(",")]) if args.params else None
+            prog, err = prepare_form(f, Ad, Bd, C, A, B, stream, pgk, torch, np, fixed)
             if err <= FORM_TOL[f]:
                 form = f
                 break
@@ -294,7 +297,7 @@ def main():
     return 0
 
 
-def prepare_form(form, Ad, Bd, C, A, B, stream, pgk, torch, np):
+def prepare_form(form, Ad, Bd, C, A, B, stream, pgk, torch, np, fixed=None):
     """Autotune the form's program parameters on the real operands and measure
     its relative Frobenius error on 64 sampled rows against the FP64 oracle."""
     import oracle
@@ -304,7 +307,10 @@ def prepare_form(form, Ad, Bd, C, A, B, stream, pgk, torch, np):
             cands = [p for p in pgk.default_candidates(dt) if p.sr > 1]
         else:
             cands = pgk.default_candidates(dt)
-        best, _ = pgk.autotune(Ad, Bd, C, dt, candidates=cands, reps=2, stream=stream)
+        if fixed is not None:
+            best = fixed
+        else:
+            best, _ = pgk.autotune(Ad, Bd, C, dt, candidates=cands, reps=2, stream=stream)
         pgk.gemm(Ad, Bd, C, dt, best, stream=stream)
     torch.cuda.synchronize()
     M = A.shape[0]
