@@ -439,8 +439,10 @@ pgk_params default_params(int M, int N, int K, pgk_dtype dtype) {
         (void)K;
     } else if (dtype == PGK_SPLIT_BF16) {
         p.B0 = 128; p.B1 = 128; p.s = 3; p.sr = 0; p.tile = 0;
-    } else {
+    } else if (dtype == PGK_BF16) {
         p.B0 = 128; p.B1 = 256; p.s = 4; p.sr = 0; p.tile = 0;
+    } else {
+        p.B0 = 128; p.B1 = 128; p.s = 6; p.sr = 0; p.tile = 0;
     }
     return p;
 }

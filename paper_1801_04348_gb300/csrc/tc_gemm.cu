@@ -1,22 +1,841 @@
-// tcgen05 tensor-core variants (placeholder until the kernels land).
+// tcgen05 tensor-core variants of the parametric GEMM for the low-precision
+// forms (BF16, split BF16, per-tile scaled FP8 E4M3), FP32 accumulation in
+// tensor memory.
+//
+// One persistent CTA per SM walks output tiles of BM x BN (BM = 128).  Warp
+// roles:
+//   warp 0  TMA producer: 128-byte-wide K slices of A (BM rows) and of B^T
+//           (BN rows) land in a STAGES-deep ring of 128B-swizzled shared tiles,
+//           completion tracked by mbarrier transaction counts;
+//   warp 1  owns the tensor-memory allocation; one thread issues tcgen05.mma
+//           (kind::f16 or kind::f8f6f4) into one of two accumulators and
+//           releases each stage with tcgen05.commit;
+//   warps 2.. epilogue: tcgen05.ld the accumulator (one TMEM lane per output
+//           row), (FP8: scale each 128-deep chunk by sA*sB and add in
+//           registers), store FP32 C, release the accumulator.
+// Every wait is bounded (globaltimer); on timeout the CTA sets the device
+// error word, stops issuing, drains its own TMA and MMA work and frees TMEM.
+//
+// Operands are K-major: A is M x K and B is given transposed (N x K), as the
+// preparation kernels write it.  Tails in M, N and K come from TMA's zero fill.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "pgk_internal.cuh"
 
 namespace pgk {
-void register_tc_variants(std::vector<Variant>&) {}
-pgk_status tc_select(const pgk_machine*, int, int, int, pgk_dtype, const pgk_params*, pgk_case*) {
-    set_error("tensor-core forms are not built yet");
+
+enum { MODE_BF16 = 0, MODE_SPLIT = 1, MODE_FP8 = 2 };
+
+static constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ULL;  // 4 s
+static constexpr unsigned int ERR_TIMEOUT_PRODUCER = 0x1u;
+static constexpr unsigned int ERR_TIMEOUT_MMA = 0x2u;
+static constexpr unsigned int ERR_TIMEOUT_EPILOGUE = 0x4u;
+static constexpr unsigned int ERR_TIMEOUT_DRAIN = 0x8u;
+
+template <int MODE_, int BN_, int STAGES_>
+struct TcCfg {
+    static constexpr int MODE = MODE_, BN = BN_, STAGES = STAGES_;
+    static constexpr int BM = 128;
+    static constexpr int BK = MODE == MODE_FP8 ? 128 : 64;   // elements per stage row (128 bytes)
+    static constexpr int UK = MODE == MODE_FP8 ? 32 : 16;    // K per MMA instruction
+    static constexpr int NKSUB = BK / UK;                   // MMAs per stage and product
+    static constexpr int A_BYTES = BM * 128;
+    static constexpr int B_BYTES = BN * 128;
+    static constexpr int NOPS = MODE == MODE_SPLIT ? 2 : 1; // hi/lo pairs
+    static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
+    static constexpr int EPI_WARPS = MODE == MODE_FP8 ? 8 : 4;
+    static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+    static constexpr int TMEM_COLS = 2 * BN;                // two FP32 accumulators
+    static constexpr int SMEM_RAW = STAGES * STAGE_BYTES + 1024;
+    // at least 116 KB so that one CTA owns the SM (and its tensor memory)
+    static constexpr int SMEM = SMEM_RAW > 118784 ? SMEM_RAW : 118784;
+    static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation is a power of two");
+    static_assert(MODE != MODE_FP8 || BN == 128, "FP8 scales are per 128 columns");
+};
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with parity `parity`.  Returns false if the CTA
+// was aborted by another warp or the limit expired (then the abort flag and
+// the device error word are set).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned int* err, unsigned int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                *abort_flag = 1;
+                atomicOr(err, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmap_prefetch(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)map) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// K-major operand tile in the canonical 128-byte swizzled layout: rows of 128
+// bytes, groups of 8 rows 1024 bytes apart (stride byte offset), tile base
+// 1024-byte aligned; version field 1 (bits 46-47), layout SWIZZLE_128B (2).
+__device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptors: D = F32 (bits 4-5 = 1), A/B formats (bits 7-9,
+// 10-12), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// 32 TMEM lanes x 32 consecutive 32-bit columns -> 32 registers per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcParams {
+    int M, N, K;
+    float* C;
+    int ldc;
+    int beta;
+    const float* sA;   // FP8: ceil(M/128) x ceil(K/128)
+    const float* sB;   // FP8: ceil(K/128) x ceil(N/128)
+    unsigned int* err;
+};
+
+template <class Cfg>
+__global__ void __launch_bounds__(Cfg::THREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
+              TcParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[Cfg::STAGES];
+    __shared__ uint64_t empty_bar[Cfg::STAGES];
+    __shared__ uint64_t accf_bar[2];
+    __shared__ uint64_t acce_bar[2];
+    __shared__ uint64_t drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+
+    const int tiles_m = (p.M + Cfg::BM - 1) / Cfg::BM;
+    const int tiles_n = (p.N + Cfg::BN - 1) / Cfg::BN;
+    const int ntiles = tiles_m * tiles_n;
+    const int nkb = (p.K + Cfg::BK - 1) / Cfg::BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf_bar[b], 1);
+            mbar_init(&acce_bar[b], Cfg::EPI_WARPS * 32);
+        }
+        mbar_init(&drain_bar, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tmap_prefetch(&tmA);
+        tmap_prefetch(&tmB);
+        if (Cfg::MODE == MODE_SPLIT) {
+            tmap_prefetch(&tmA2);
+            tmap_prefetch(&tmB2);
+        }
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"((uint32_t)Cfg::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+    volatile int* abort_flag = &abort_sh;
+
+    // tile t -> (tm, tn): groups of 16 tile-rows walked column by column
+    auto coords = [&](int t, int& tm, int& tn) {
+        const int G = 16;
+        const int per = G * tiles_n;
+        const int g = t / per;
+        const int first = g * G;
+        const int gm = min(tiles_m - first, G);
+        const int r = t - g * per;
+        tm = first + r % gm;
+        tn = r / gm;
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------- producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued_mask = 0, last_parity = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                int tm, tn;
+                coords(t, tm, tn);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(&empty_bar[stage], phase ^ 1u, abort_flag, p.err,
+                                   ERR_TIMEOUT_PRODUCER)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = tiles + (size_t)stage * Cfg::STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full_bar[stage], Cfg::STAGE_BYTES);
+                    const int x = kb * Cfg::BK;
+                    tma_load_2d(st, &tmA, &full_bar[stage], x, tm * Cfg::BM);
+                    tma_load_2d(st + Cfg::A_BYTES, &tmB, &full_bar[stage], x, tn * Cfg::BN);
+                    if (Cfg::MODE == MODE_SPLIT) {
+                        tma_load_2d(st + Cfg::A_BYTES + Cfg::B_BYTES, &tmA2, &full_bar[stage], x,
+                                    tm * Cfg::BM);
+                        tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tmB2, &full_bar[stage],
+                                    x, tn * Cfg::BN);
+                    }
+                    issued_mask |= 1u << stage;
+                    last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+                    if (++stage == Cfg::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // drain: every issued copy must land before the CTA may exit
+                for (int s = 0; s < Cfg::STAGES; ++s)
+                    if (issued_mask & (1u << s)) {
+                        const unsigned long long t0 = globaltimer();
+                        while (!mbar_try_wait(&full_bar[s], (last_parity >> s) & 1u)) {
+                            if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                                atomicOr(p.err, ERR_TIMEOUT_DRAIN);
+                                break;
+                            }
+                        }
+                    }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA
+        if (lane == 0) {
+            const uint32_t idesc = Cfg::MODE == MODE_FP8 ? idesc_e4m3(Cfg::BM, Cfg::BN)
+                                                         : idesc_bf16(Cfg::BM, Cfg::BN);
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            bool issued_any = false;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                if (Cfg::MODE != MODE_FP8) {
+                    if (!mbar_wait(&acce_bar[acc], acc_phase ^ 1u, abort_flag, p.err, ERR_TIMEOUT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (Cfg::MODE == MODE_FP8) {
+                        // one accumulator per 128-deep chunk, promoted by the epilogue
+                        if (!mbar_wait(&acce_bar[acc], acc_phase ^ 1u, abort_flag, p.err,
+                                       ERR_TIMEOUT_MMA)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    if (!mbar_wait(&full_bar[stage], phase, abort_flag, p.err, ERR_TIMEOUT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + (uint32_t)(acc * Cfg::BN);
+                    const uint32_t sa = smem_u32(tiles + (size_t)stage * Cfg::STAGE_BYTES);
+                    const uint32_t sb = sa + Cfg::A_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < Cfg::NKSUB; ++ks) {
+                        const uint32_t koff = (uint32_t)ks * 32u;  // 32 bytes of K per MMA
+                        const uint64_t da = sdesc_k128(sa + koff);
+                        const uint64_t db = sdesc_k128(sb + koff);
+                        if (Cfg::MODE == MODE_FP8) {
+                            mma_f8(d, da, db, idesc, ks > 0 ? 1u : 0u);
+                        } else if (Cfg::MODE == MODE_BF16) {
+                            mma_f16(d, da, db, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+                        } else {
+                            const uint32_t sa2 = sb + Cfg::B_BYTES;   // A lo
+                            const uint32_t sb2 = sa2 + Cfg::A_BYTES;  // B lo
+                            const uint64_t da2 = sdesc_k128(sa2 + koff);
+                            const uint64_t db2 = sdesc_k128(sb2 + koff);
+                            // small terms first: lo*hi, hi*lo, then hi*hi
+                            mma_f16(d, da2, db, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+                            mma_f16(d, da, db2, idesc, 1u);
+                            mma_f16(d, da, db, idesc, 1u);
+                        }
+                    }
+                    issued_any = true;
+                    mma_commit(&empty_bar[stage]);
+                    if (++stage == Cfg::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                    if (Cfg::MODE == MODE_FP8) {
+                        mma_commit(&accf_bar[acc]);
+                        if (++acc == 2) {
+                            acc = 0;
+                            acc_phase ^= 1u;
+                        }
+                    }
+                }
+                if (!ok) break;
+                if (Cfg::MODE != MODE_FP8) {
+                    mma_commit(&accf_bar[acc]);
+                    if (++acc == 2) {
+                        acc = 0;
+                        acc_phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok && issued_any) {
+                // drain: all MMAs issued by this thread must finish before TMEM is freed
+                mma_commit(&drain_bar);
+                const unsigned long long t0 = globaltimer();
+                while (!mbar_try_wait(&drain_bar, 0)) {
+                    if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                        atomicOr(p.err, ERR_TIMEOUT_DRAIN);
+                        break;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // -------------------------------------------------------- epilogue
+        const int e = warp - 2;
+        const int q = warp & 3;                       // TMEM lane quarter of this warp
+        const int ncol = Cfg::BN / (Cfg::EPI_WARPS / 4);  // columns handled by this warp
+        const int col0 = (e >> 2) * ncol;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            int tm, tn;
+            coords(t, tm, tn);
+            const int row = tm * Cfg::BM + q * 32 + lane;
+            const int n0 = tn * Cfg::BN + col0;
+            float* crow = p.C + (size_t)row * p.ldc;
+            const bool row_ok = row < p.M;
+            const bool vec = ((p.ldc & 3) == 0) && ((((uintptr_t)p.C) & 15u) == 0);
+            if (Cfg::MODE == MODE_FP8) {
+                float accr[Cfg::BN / (Cfg::EPI_WARPS / 4)];
+#pragma unroll
+                for (int j = 0; j < ncol; ++j) accr[j] = 0.f;
+                const int ksa = (p.K + 127) / 128, nsb = (p.N + 127) / 128;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    int w = 1;
+                    if (lane == 0)
+                        w = mbar_wait(&accf_bar[acc], acc_phase, abort_flag, p.err,
+                                      ERR_TIMEOUT_EPILOGUE) ? 1 : 0;
+                    w = __shfl_sync(0xffffffffu, w, 0);
+                    if (!w) {
+                        ok = false;
+                        break;
+                    }
+                    while (!mbar_try_wait(&accf_bar[acc], acc_phase)) {
+                    }
+                    tc_fence_after();
+                    const float sc = __ldg(p.sA + (size_t)tm * ksa + kb) * __ldg(p.sB + (size_t)kb * nsb + tn);
+#pragma unroll
+                    for (int c = 0; c < ncol / 32; ++c) {
+                        uint32_t r[32];
+                        tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) +
+                                      (uint32_t)(acc * Cfg::BN + col0 + c * 32),
+                                  r);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            accr[c * 32 + j] = fmaf(__uint_as_float(r[j]), sc, accr[c * 32 + j]);
+                    }
+                    tc_fence_before();
+                    mbar_arrive(&acce_bar[acc]);
+                    if (++acc == 2) {
+                        acc = 0;
+                        acc_phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                if (row_ok) {
+#pragma unroll
+                    for (int j = 0; j < ncol; j += 4) {
+                        const int n = n0 + j;
+                        if (vec && n + 3 < p.N) {
+                            float4 o = make_float4(accr[j], accr[j + 1], accr[j + 2], accr[j + 3]);
+                            if (p.beta) {
+                                const float4 c = *reinterpret_cast<const float4*>(crow + n);
+                                o.x += c.x; o.y += c.y; o.z += c.z; o.w += c.w;
+                            }
+                            *reinterpret_cast<float4*>(crow + n) = o;
+                        } else {
+                            for (int u = 0; u < 4; ++u)
+                                if (n + u < p.N)
+                                    crow[n + u] = p.beta ? crow[n + u] + accr[j + u] : accr[j + u];
+                        }
+                    }
+                }
+            } else {
+                int w = 1;
+                if (lane == 0)
+                    w = mbar_wait(&accf_bar[acc], acc_phase, abort_flag, p.err, ERR_TIMEOUT_EPILOGUE)
+                            ? 1 : 0;
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (!w) {
+                    ok = false;
+                    break;
+                }
+                while (!mbar_try_wait(&accf_bar[acc], acc_phase)) {
+                }
+                tc_fence_after();
+#pragma unroll 1
+                for (int c = 0; c < ncol / 32; ++c) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) +
+                                  (uint32_t)(acc * Cfg::BN + col0 + c * 32),
+                              r);
+                    tmem_ld_wait();
+                    if (row_ok) {
+                        const int nb = n0 + c * 32;
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            const int n = nb + j;
+                            if (vec && n + 3 < p.N) {
+                                float4 o = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                       __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                                if (p.beta) {
+                                    const float4 cc = *reinterpret_cast<const float4*>(crow + n);
+                                    o.x += cc.x; o.y += cc.y; o.z += cc.z; o.w += cc.w;
+                                }
+                                *reinterpret_cast<float4*>(crow + n) = o;
+                            } else {
+                                for (int u = 0; u < 4; ++u)
+                                    if (n + u < p.N) {
+                                        const float v = __uint_as_float(r[j + u]);
+                                        crow[n + u] = p.beta ? crow[n + u] + v : v;
+                                    }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&acce_bar[acc]);
+                if (++acc == 2) {
+                    acc = 0;
+                    acc_phase ^= 1u;
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"((uint32_t)Cfg::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------ host side
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::mutex g_tc_mu;
+
+static pgk_status get_encoder() {
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    if (g_encode) return PGK_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        if (e != cudaSuccess) cudaGetLastError();
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return PGK_ERR_CUDA;
+    }
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return PGK_OK;
+}
+
+// 2D K-major tensor map: rows x K elements, row stride ld elements, box
+// (128 bytes of K) x box_rows, 128-byte swizzle, zero fill out of bounds.
+static pgk_status make_map(CUtensorMap* map, const void* base, int rows, int K, int ld, int esz,
+                           int box_rows) {
+    if (((uintptr_t)base & 15u) != 0 || ((long long)ld * esz) % 16 != 0) {
+        set_error("tensor-core operand must be 16-byte aligned with a row stride multiple of 16 bytes");
+        return PGK_ERR_ALIGNMENT;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                          2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for rows=%d K=%d ld=%d", (int)r, rows, K, ld);
+        return PGK_ERR_CUDA;
+    }
+    return PGK_OK;
+}
+
+typedef cudaError_t (*tc_launch_fn)(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&,
+                                    const CUtensorMap&, const TcParams&, int grid, cudaStream_t);
+
+template <class Cfg>
+static cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& a2,
+                             const CUtensorMap& b2, const TcParams& p, int grid, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_tc_gemm<Cfg>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<Cfg><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a, b, a2, b2, p);
+    return cudaGetLastError();
+}
+
+struct TcVariant {
+    int family, BN, stages, smem, threads, tmem_cols;
+    const void* func;
+    tc_launch_fn launch;
+};
+
+template <int MODE, int BN, int ST>
+static TcVariant tcv(int family) {
+    typedef TcCfg<MODE, BN, ST> Cfg;
+    TcVariant v = {family, BN, ST, Cfg::SMEM, Cfg::THREADS, Cfg::TMEM_COLS,
+                   (const void*)k_tc_gemm<Cfg>, launch_tc<Cfg>};
+    return v;
+}
+
+static const TcVariant* tc_table(int* n) {
+    static const TcVariant t[] = {
+        tcv<MODE_BF16, 256, 4>(PGK_FAM_TC_BF16),   tcv<MODE_BF16, 128, 6>(PGK_FAM_TC_BF16),
+        tcv<MODE_SPLIT, 128, 3>(PGK_FAM_TC_SPLIT), tcv<MODE_SPLIT, 256, 2>(PGK_FAM_TC_SPLIT),
+        tcv<MODE_FP8, 128, 6>(PGK_FAM_TC_FP8),     tcv<MODE_FP8, 128, 4>(PGK_FAM_TC_FP8),
+    };
+    *n = (int)(sizeof(t) / sizeof(t[0]));
+    return t;
+}
+
+static int tc_base_id = -1;  // registry index of the first tensor-core variant
+
+void register_tc_variants(std::vector<Variant>& v) {
+    int n;
+    const TcVariant* t = tc_table(&n);
+    tc_base_id = (int)v.size();
+    for (int i = 0; i < n; ++i) {
+        Variant x;
+        x.info.family = t[i].family;
+        x.info.s = t[i].stages;
+        x.info.sr = 0;
+        x.info.B0 = 128;
+        x.info.B1 = t[i].BN;
+        x.info.tile = 0;
+        x.info.regopt = 0;
+        x.info.regs = -1;
+        x.info.max_threads = -1;
+        x.func = t[i].func;
+        x.launch = nullptr;
+        x.smem_fixed = t[i].smem;
+        v.push_back(x);
+    }
+}
+
+static int family_of(pgk_dtype d) {
+    return d == PGK_BF16 ? PGK_FAM_TC_BF16 : d == PGK_SPLIT_BF16 ? PGK_FAM_TC_SPLIT : PGK_FAM_TC_FP8;
+}
+
+pgk_status tc_select(const pgk_machine* m, int M, int N, int K, pgk_dtype dtype,
+                     const pgk_params* prog, pgk_case* out) {
+    (void)M; (void)N; (void)K;
+    registry();
+    int n;
+    const TcVariant* t = tc_table(&n);
+    const int fam = family_of(dtype);
+    const int natural = dtype == PGK_FP8_E4M3 ? 128 : 64;
+    if (prog->B0 != 128 || (prog->tile != 0 && prog->tile != natural) || prog->s < 1) {
+        set_error("tensor-core tiles are 128 x B1 with the natural K depth (B0=%d tile=%d)", prog->B0,
+                  prog->tile);
+        return PGK_ERR_UNSUPPORTED;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (t[i].family != fam || t[i].BN != prog->B1 || t[i].stages != prog->s) continue;
+        // resource counters of the variant against the machine parameters
+        if (t[i].threads > m->max_threads_per_block || t[i].smem > m->smem_per_block_optin ||
+            t[i].tmem_cols > 512 || m->cc_major != 10) {
+            set_error("tensor-core variant does not fit this device (smem %d > %d or cc %d.%d)",
+                      t[i].smem, m->smem_per_block_optin, m->cc_major, m->cc_minor);
+            return PGK_ERR_INFEASIBLE;
+        }
+        pgk_case c;
+        memset(&c, 0, sizeof(c));
+        c.leaf = PGK_LEAF_4A3A;
+        c.variant_id = tc_base_id + i;
+        c.family = fam;
+        c.smem_bytes = t[i].smem;
+        c.regs = -1;
+        c.threads = t[i].threads;
+        c.params = *prog;
+        c.params.tile = natural;
+        c.params.sr = 0;
+        *out = c;
+        return PGK_OK;
+    }
+    set_error("no tensor-core variant with B1=%d stages=%d for this form", prog->B1, prog->s);
     return PGK_ERR_UNSUPPORTED;
 }
-pgk_status tc_gemm_fp32_inputs(const pgk_case&, int, int, int, pgk_dtype, const float*, int,
-                               const float*, int, float*, int, int, cudaStream_t) {
-    set_error("tensor-core forms are not built yet");
-    return PGK_ERR_UNSUPPORTED;
+
+pgk_status tc_gemm_launch(const pgk_case& c, int M, int N, int K, pgk_dtype dtype, const void* A,
+                          int lda, const void* Bt, int ldbt, const void* A_lo, const void* Bt_lo,
+                          const float* sA, const float* sB, float* C, int ldc, int beta,
+                          cudaStream_t stream) {
+    pgk_status st = get_encoder();
+    if (st != PGK_OK) return st;
+    int n;
+    const TcVariant* t = tc_table(&n);
+    const int i = c.variant_id - tc_base_id;
+    if (i < 0 || i >= n || t[i].family != family_of(dtype)) {
+        set_error("case does not name a tensor-core variant of this form");
+        return PGK_ERR_INVALID_ARG;
+    }
+    const int esz = dtype == PGK_FP8_E4M3 ? 1 : 2;
+    CUtensorMap ma, mb, ma2, mb2;
+    if ((st = make_map(&ma, A, M, K, lda, esz, 128)) != PGK_OK) return st;
+    if ((st = make_map(&mb, Bt, N, K, ldbt, esz, t[i].BN)) != PGK_OK) return st;
+    if (dtype == PGK_SPLIT_BF16) {
+        if (!A_lo || !Bt_lo) {
+            set_error("split form needs the lo operands");
+            return PGK_ERR_INVALID_ARG;
+        }
+        if ((st = make_map(&ma2, A_lo, M, K, lda, esz, 128)) != PGK_OK) return st;
+        if ((st = make_map(&mb2, Bt_lo, N, K, ldbt, esz, t[i].BN)) != PGK_OK) return st;
+    } else {
+        ma2 = ma;
+        mb2 = mb;
+    }
+    if (dtype == PGK_FP8_E4M3 && (!sA || !sB)) {
+        set_error("FP8 form needs the tile scales");
+        return PGK_ERR_INVALID_ARG;
+    }
+    pgk_machine m;
+    if ((st = current_machine(&m, NULL)) != PGK_OK) return st;
+    TcParams p;
+    p.M = M;
+    p.N = N;
+    p.K = K;
+    p.C = C;
+    p.ldc = ldc;
+    p.beta = beta ? 1 : 0;
+    p.sA = sA;
+    p.sB = sB;
+    p.err = device_error_word(&st);
+    if (!p.err) return st;
+    const long long tiles = (long long)((M + 127) / 128) * ((N + t[i].BN - 1) / t[i].BN);
+    const int grid = (int)std::min<long long>(tiles, m.sm_count);
+    cudaError_t e = t[i].launch(ma, mb, ma2, mb2, p, grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
+    return PGK_OK;
 }
+
+pgk_status launch_cvt_bf16(int rows, int cols, const float* src, int lds, uint16_t* dst, int ldd,
+                           int transpose, cudaStream_t st);
+pgk_status launch_split_bf16(int rows, int cols, const float* src, int lds, uint16_t* hi,
+                             uint16_t* lo, int ldd, int transpose, cudaStream_t st);
+pgk_status launch_quant_fp8(int rows, int cols, const float* src, int lds, uint8_t* dst, int ldd,
+                            float* scales, int ld_scales, int transpose, cudaStream_t st);
+
+// FP32 operands -> library workspaces (K padded to a multiple of 16 elements)
+// -> tensor-core kernel.
+pgk_status tc_gemm_fp32_inputs(const pgk_case& c, int M, int N, int K, pgk_dtype dtype,
+                               const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                               int beta, cudaStream_t s) {
+    const int Kp = (K + 15) / 16 * 16;
+    const int esz = dtype == PGK_FP8_E4M3 ? 1 : 2;
+    pgk_status st;
+    void* a0 = workspace(WS_A0, (size_t)M * Kp * esz, &st);
+    if (!a0) return st;
+    void* b0 = workspace(WS_B0, (size_t)N * Kp * esz, &st);
+    if (!b0) return st;
+    if (dtype == PGK_BF16) {
+        if ((st = launch_cvt_bf16(M, K, A, lda, (uint16_t*)a0, Kp, 0, s)) != PGK_OK) return st;
+        if ((st = launch_cvt_bf16(K, N, B, ldb, (uint16_t*)b0, Kp, 1, s)) != PGK_OK) return st;
+        return tc_gemm_launch(c, M, N, K, dtype, a0, Kp, b0, Kp, nullptr, nullptr, nullptr, nullptr,
+                              C, ldc, beta, s);
+    }
+    if (dtype == PGK_SPLIT_BF16) {
+        void* a1 = workspace(WS_A1, (size_t)M * Kp * 2, &st);
+        if (!a1) return st;
+        void* b1 = workspace(WS_B1, (size_t)N * Kp * 2, &st);
+        if (!b1) return st;
+        if ((st = launch_split_bf16(M, K, A, lda, (uint16_t*)a0, (uint16_t*)a1, Kp, 0, s)) != PGK_OK)
+            return st;
+        if ((st = launch_split_bf16(K, N, B, ldb, (uint16_t*)b0, (uint16_t*)b1, Kp, 1, s)) != PGK_OK)
+            return st;
+        return tc_gemm_launch(c, M, N, K, dtype, a0, Kp, b0, Kp, a1, b1, nullptr, nullptr, C, ldc,
+                              beta, s);
+    }
+    const int mt = (M + 127) / 128, kt = (K + 127) / 128, nt = (N + 127) / 128;
+    float* sa = (float*)workspace(WS_SA, (size_t)mt * kt * 4, &st);
+    if (!sa) return st;
+    float* sb = (float*)workspace(WS_SB, (size_t)kt * nt * 4, &st);
+    if (!sb) return st;
+    if ((st = launch_quant_fp8(M, K, A, lda, (uint8_t*)a0, Kp, sa, kt, 0, s)) != PGK_OK) return st;
+    if ((st = launch_quant_fp8(K, N, B, ldb, (uint8_t*)b0, Kp, sb, nt, 1, s)) != PGK_OK) return st;
+    return tc_gemm_launch(c, M, N, K, dtype, a0, Kp, b0, Kp, nullptr, nullptr, sa, sb, C, ldc, beta,
+                          s);
+}
+
 }  // namespace pgk
 
-extern "C" pgk_status pgk_gemm_lowp(int, int, int, pgk_dtype, const void*, int, const void*, int,
-                                    const void*, const void*, const float*, const float*, float*,
-                                    int, int, const pgk_params*, void*) {
-    pgk::set_error("tensor-core forms are not built yet");
-    return PGK_ERR_UNSUPPORTED;
+using namespace pgk;
+
+extern "C" pgk_status pgk_gemm_lowp(int M, int N, int K, pgk_dtype dtype, const void* A, int lda,
+                                    const void* Bt, int ldbt, const void* A_lo, const void* Bt_lo,
+                                    const float* scaleA, const float* scaleB, float* C, int ldc,
+                                    int beta, const pgk_params* prog, void* stream) {
+    if (M < 1 || N < 1 || K < 1 || !A || !Bt || !C || lda < K || ldbt < K || ldc < N) {
+        set_error("bad tensor-core GEMM arguments");
+        return PGK_ERR_INVALID_ARG;
+    }
+    if (dtype != PGK_BF16 && dtype != PGK_SPLIT_BF16 && dtype != PGK_FP8_E4M3) {
+        set_error("pgk_gemm_lowp takes the BF16, split-BF16 or FP8 forms");
+        return PGK_ERR_INVALID_ARG;
+    }
+    pgk_machine m;
+    pgk_status st = current_machine(&m, NULL);
+    if (st != PGK_OK) return st;
+    pgk_params p;
+    if (prog) {
+        p = *prog;
+    } else if (pgk_tune_cache_get(M, N, K, dtype, &p) != PGK_OK) {
+        pgk_params d = {128, dtype == PGK_SPLIT_BF16 ? 128 : (dtype == PGK_BF16 ? 256 : 128),
+                        dtype == PGK_SPLIT_BF16 ? 3 : (dtype == PGK_BF16 ? 4 : 6), 0, 0};
+        p = d;
+    }
+    pgk_case c;
+    st = tc_select(&m, M, N, K, dtype, &p, &c);
+    if (st != PGK_OK) return st;
+    return tc_gemm_launch(c, M, N, K, dtype, A, lda, Bt, ldbt, A_lo, Bt_lo, scaleA, scaleB, C, ldc,
+                          beta, (cudaStream_t)stream);
 }

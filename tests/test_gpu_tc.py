@@ -1,0 +1,215 @@
+"""Parity of the low-precision operand preparation (bit-exact) and of the
+tcgen05 tensor-core GEMM forms (BF16, split BF16, per-tile FP8) with the
+oracle, through the C ABI on the GPU."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import quant
+from paper_1801_04348_gb300 import inputs, pgk
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = {pgk.BF16: [(256, 4), (128, 6)], pgk.SPLIT_BF16: [(128, 3), (256, 2)],
+            pgk.FP8_E4M3: [(128, 6), (128, 4)]}
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import __graft_entry__
+    __graft_entry__.build()
+    d = torch.device("cuda:0")
+    torch.cuda.set_device(d)
+    return d
+
+
+def _t(x, dev):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+def _kpad(K):
+    return (K + 15) // 16 * 16
+
+
+def prep(dev, A, B, form):
+    """Prepared operands through the library's preparation entry points."""
+    M, K = A.shape
+    N = B.shape[1]
+    Kp = _kpad(K)
+    At, Bt = _t(A, dev), _t(B, dev)
+    if form == pgk.BF16:
+        a = torch.zeros(M, Kp, dtype=torch.int16, device=dev)
+        b = torch.zeros(N, Kp, dtype=torch.int16, device=dev)
+        pgk.cvt_bf16(At, a, 0)
+        pgk.cvt_bf16(Bt, b, 1)
+        return dict(A=a, Bt=b)
+    if form == pgk.SPLIT_BF16:
+        a = torch.zeros(M, Kp, dtype=torch.int16, device=dev)
+        al = torch.zeros_like(a)
+        b = torch.zeros(N, Kp, dtype=torch.int16, device=dev)
+        bl = torch.zeros_like(b)
+        pgk.split_bf16(At, a, al, 0)
+        pgk.split_bf16(Bt, b, bl, 1)
+        return dict(A=a, Bt=b, A_lo=al, Bt_lo=bl)
+    a = torch.zeros(M, Kp, dtype=torch.uint8, device=dev)
+    b = torch.zeros(N, Kp, dtype=torch.uint8, device=dev)
+    sa = torch.zeros((M + 127) // 128, (K + 127) // 128, device=dev)
+    sb = torch.zeros((K + 127) // 128, (N + 127) // 128, device=dev)
+    pgk.quant_fp8(At, a, sa, 0)
+    pgk.quant_fp8(Bt, b, sb, 1)
+    return dict(A=a, Bt=b, scaleA=sa, scaleB=sb)
+
+
+def run_lowp(dev, form, ops, M, N, K, prog=None, beta=0, C0=None):
+    C = _t(C0, dev) if C0 is not None else torch.full((M, N), float("nan"), device=dev)
+    Kp = ops["A"].stride(0)
+    pgk.gemm_lowp(M, N, K, form, ops["A"], Kp, ops["Bt"], Kp, C, N, A_lo=ops.get("A_lo"),
+                  Bt_lo=ops.get("Bt_lo"), scaleA=ops.get("scaleA"), scaleB=ops.get("scaleB"),
+                  beta=beta, prog=prog)
+    torch.cuda.synchronize()
+    pgk.check_device_error()
+    return C.cpu().numpy()
+
+
+def _u16(t):
+    return t.cpu().numpy().view(np.uint16)
+
+
+# ------------------------------------------------------------- preparation
+@pytest.mark.parametrize("R,Cc", [(300, 200), (1, 1), (129, 257), (64, 1000)])
+def test_cvt_bf16_bit_exact(dev, R, Cc):
+    X = np.concatenate([inputs.normal((R * Cc,), 1)[: R * Cc // 2] * 1e3,
+                        inputs.uniform((R * Cc - R * Cc // 2,), 2) * 1e-30]).reshape(R, Cc).astype(np.float32)
+    Xt = _t(X, dev)
+    d = torch.zeros(R, Cc + 5, dtype=torch.int16, device=dev)
+    pgk.cvt_bf16(Xt, d, 0)
+    assert np.array_equal(_u16(d)[:, :Cc], quant.bf16_bits(X))
+    dt = torch.zeros(Cc, R + 3, dtype=torch.int16, device=dev)
+    pgk.cvt_bf16(Xt, dt, 1)
+    assert np.array_equal(_u16(dt)[:, :R], quant.bf16_bits(X).T)
+
+
+def test_split_bf16_bit_exact(dev):
+    X = inputs.normal((333, 190), 3) * np.float32(3.7)
+    hi_ref, lo_ref = quant.split_bf16(X)
+    Xt = _t(X, dev)
+    for tr in (0, 1):
+        shape = (333, 192) if tr == 0 else (190, 336)
+        hi = torch.zeros(*shape, dtype=torch.int16, device=dev)
+        lo = torch.zeros_like(hi)
+        pgk.split_bf16(Xt, hi, lo, tr)
+        h, l = _u16(hi), _u16(lo)
+        if tr:
+            h, l = h[:, :333].T, l[:, :333].T
+        else:
+            h, l = h[:, :190], l[:, :190]
+        assert np.array_equal(quant.bf16_from_bits(h), hi_ref)
+        assert np.array_equal(quant.bf16_from_bits(l), lo_ref)
+
+
+@pytest.mark.parametrize("R,Cc", [(300, 200), (128, 128), (1, 5), (257, 383)])
+def test_quant_fp8_bit_exact(dev, R, Cc):
+    X = inputs.normal((R, Cc), 4) * inputs.row_factors(R, 5, 2.0)[:, None]
+    X = X.astype(np.float32)
+    codes, S = quant.fp8_tile_quant(X)
+    Xt = _t(X, dev)
+    q = torch.zeros(R, _kpad(Cc), dtype=torch.uint8, device=dev)
+    s = torch.zeros((R + 127) // 128, (Cc + 127) // 128, device=dev)
+    pgk.quant_fp8(Xt, q, s, 0)
+    assert np.array_equal(s.cpu().numpy(), S)
+    assert np.array_equal(q.cpu().numpy()[:, :Cc], codes)
+    qt = torch.zeros(Cc, _kpad(R), dtype=torch.uint8, device=dev)
+    pgk.quant_fp8(Xt, qt, s, 1)
+    assert np.array_equal(qt.cpu().numpy()[:, :R], codes.T)
+
+
+# --------------------------------------------------------------- GEMMs
+@pytest.mark.parametrize("form", [pgk.BF16, pgk.SPLIT_BF16, pgk.FP8_E4M3])
+def test_integer_inputs_exact(dev, form):
+    """Small integers are exact in every format (FP8: |x| <= 7 with a 7 in every
+    tile makes the scale 2^-6); products and FP32 sums are exact, so the tensor
+    cores must reproduce the oracle bit for bit, for every compiled variant."""
+    M, N, K = 256, 384, 512
+    lo, hi = (-7, 7) if form == pgk.FP8_E4M3 else (-8, 8)
+    A = inputs.integers((M, K), 7, lo, hi)
+    B = inputs.integers((K, N), 8, lo, hi)
+    if form == pgk.FP8_E4M3:
+        A[::128, ::128] = 7
+        B[::128, ::128] = 7
+    ref = oracle.gemm(A, B)
+    ops = prep(dev, A, B, form)
+    for bn, st in VARIANTS[form]:
+        C = run_lowp(dev, form, ops, M, N, K, pgk.params(128, bn, st, 0, 0))
+        assert np.array_equal(C.astype(np.float64), ref), (form, bn, st)
+
+
+@pytest.mark.parametrize("form", [pgk.BF16, pgk.SPLIT_BF16, pgk.FP8_E4M3])
+@pytest.mark.parametrize("M,N,K", [(200, 168, 136), (1, 1, 1), (129, 255, 1000), (640, 520, 64)])
+def test_ragged_against_dequantised_oracle(dev, form, M, N, K):
+    """Against the FP64 product of the dequantised operands the only error left
+    is FP32 accumulation (and, for FP8, the chunk scaling): tight bound."""
+    A, B = inputs.gemm_operands(M, N, K, seed=M + 3 * N + 7 * K, dist="normal")
+    ops = prep(dev, A, B, form)
+    if form == pgk.BF16:
+        Ad, Bd = quant.bf16_rn(A).astype(np.float64), quant.bf16_rn(B).astype(np.float64)
+    elif form == pgk.SPLIT_BF16:
+        ha, la = quant.split_bf16(A)
+        hb, lb = quant.split_bf16(B)
+        Ad = None
+    else:
+        ca, sa = quant.fp8_tile_quant(A)
+        cbt, sbt = quant.fp8_tile_quant(B)
+        Ad, Bd = quant.fp8_dequant(ca, sa), quant.fp8_dequant(cbt, sbt)
+    if form == pgk.SPLIT_BF16:
+        h = lambda x: x.astype(np.float64)
+        ref = oracle.gemm(h(ha), h(hb)) + oracle.gemm(h(ha), h(lb)) + oracle.gemm(h(la), h(hb))
+    else:
+        ref = oracle.gemm(Ad, Bd)
+    absab = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64)
+    for bn, st in VARIANTS[form]:
+        C = run_lowp(dev, form, ops, M, N, K, pgk.params(128, bn, st, 0, 0)).astype(np.float64)
+        # FP32 accumulation of K products (3K for split): gamma bound on |A||B|
+        k_eff = 3 * K if form == pgk.SPLIT_BF16 else K
+        bound = (k_eff + 2) * 2.0 ** -24 * absab * 2.5 + 1e-30
+        assert np.all(np.abs(C - ref) <= bound), (form, bn, st)
+
+
+TOL = {pgk.BF16: 2e-2, pgk.SPLIT_BF16: 2e-5, pgk.FP8_E4M3: 5e-2}
+
+
+@pytest.mark.parametrize("form", [pgk.BF16, pgk.SPLIT_BF16, pgk.FP8_E4M3])
+def test_fp32_inputs_tolerance_and_beta(dev, form):
+    """pgk_gemm on FP32 inputs (library-side preparation) meets the form's
+    relative Frobenius tolerance against the FP64 oracle, also with beta = 1."""
+    M, N, K = 520, 392, 1032
+    A, B = inputs.gemm_operands(M, N, K, seed=21, dist="normal")
+    C0 = inputs.normal((M, N), 22)
+    At, Bt = _t(A, dev), _t(B, dev)
+    C = _t(C0, dev)
+    pgk.gemm(At, Bt, C, form, None, beta=1)
+    torch.cuda.synchronize()
+    pgk.check_device_error()
+    ref = oracle.gemm(A, B, C0=C0.astype(np.float64), beta=1.0)
+    err = oracle.rel_frobenius(C.cpu().numpy(), ref)
+    assert err <= TOL[form], err
+
+
+@pytest.mark.parametrize("dist", ["normal", "normal_rowscaled"])
+@pytest.mark.parametrize("form", [pgk.BF16, pgk.SPLIT_BF16, pgk.FP8_E4M3])
+def test_full_size_8192_sampled_rows(dev, form, dist):
+    """M = N = K = 8192 (the precision workload), normal(0,1) and row-scaled
+    inputs; 32 sampled rows against the FP64 oracle; the error is printed."""
+    M = N = K = 8192
+    A, B = inputs.gemm_operands(M, N, K, seed=0, dist=dist)
+    At, Bt = _t(A, dev), _t(B, dev)
+    C = torch.empty(M, N, device=dev)
+    pgk.gemm(At, Bt, C, form, None)
+    torch.cuda.synchronize()
+    pgk.check_device_error()
+    rows = np.linspace(0, M - 1, 32).astype(np.int64)
+    ref = oracle.gemm(A, B, rows=rows)
+    err = oracle.rel_frobenius(C[torch.from_numpy(rows).to(dev)].cpu().numpy(), ref)
+    print(f"form={form} dist={dist} rel_frobenius={err:.3e}")
+    if dist == "normal":
+        assert err <= TOL[form], err
