@@ -298,6 +298,19 @@ PGK_API pgk_status pgk_autotune(int M, int N, int K, pgk_dtype dtype, const floa
                         const pgk_params* candidates, int ncand, int reps,
                         float* ms_out, pgk_params* best, const char* log_path, void* stream);
 
+/* Grouped tile variants compiled for pgk_gemm_grouped (host array of `cap`
+ * entries, may be NULL); *count receives the number available. */
+PGK_API pgk_status pgk_grouped_variants(pgk_params* out, int cap, int* count);
+
+/* Time each grouped tile variant (candidates NULL = all compiled ones) on the
+ * given problems (their C is overwritten) and store the fastest as the
+ * default of pgk_gemm_grouped(prog = NULL) for groups of G problems.
+ * ms_out (host, may be NULL) gets each candidate's median time.  Synchronises.
+ * Errors: INVALID_ARG, INFEASIBLE, CUDA. */
+PGK_API pgk_status pgk_autotune_grouped(int G, const pgk_problem* problems,
+                                        const pgk_params* candidates, int ncand, int reps,
+                                        float* ms_out, pgk_params* best, void* stream);
+
 /* Number of built-in candidates of a form (the autotuner's default set). */
 PGK_API int pgk_default_candidates(pgk_dtype dtype, pgk_params* out, int cap);
 

@@ -50,14 +50,19 @@ struct TcCfg {
     static constexpr int B_BYTES = BN * 128;
     static constexpr int NOPS = MODE == MODE_SPLIT ? 2 : 1; // hi/lo pairs
     static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
-    static constexpr int EPI_WARPS = MODE == MODE_FP8 ? 8 : 4;
+    // K blocks accumulated in tensor memory before the epilogue folds the chunk
+    // into FP32 registers (0 = whole K in tensor memory).  FP8: every 128-deep
+    // chunk carries its own scales.  Split: 512-deep chunks bound the growth
+    // of the tensor-core accumulator, the dominant error at large K.
+    static constexpr int CHUNK = MODE == MODE_FP8 ? 1 : (MODE == MODE_SPLIT ? 8 : 0);
+    static constexpr int EPI_WARPS = CHUNK == 0 ? 4 : (BN == 256 ? 16 : 8);
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
     static constexpr int TMEM_COLS = 2 * BN;                // two FP32 accumulators
     static constexpr int SMEM_RAW = STAGES * STAGE_BYTES + 1024;
     // at least 116 KB so that one CTA owns the SM (and its tensor memory)
     static constexpr int SMEM = SMEM_RAW > 118784 ? SMEM_RAW : 118784;
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation is a power of two");
-    static_assert(MODE != MODE_FP8 || BN == 128, "FP8 scales are per 128 columns");
+    static_assert(CHUNK == 0 || BN / (EPI_WARPS / 4) == 64, "64 promoted columns per warp");
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -341,7 +346,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             bool ok = true;
             bool issued_any = false;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                if (Cfg::MODE != MODE_FP8) {
+                if (Cfg::CHUNK == 0) {
                     if (!mbar_wait(&acce_bar[acc], acc_phase ^ 1u, abort_flag, p.err, ERR_TIMEOUT_MMA)) {
                         ok = false;
                         break;
@@ -349,8 +354,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     tc_fence_after();
                 }
                 for (int kb = 0; kb < nkb; ++kb) {
-                    if (Cfg::MODE == MODE_FP8) {
-                        // one accumulator per 128-deep chunk, promoted by the epilogue
+                    const int kin = Cfg::CHUNK > 0 ? kb % Cfg::CHUNK : kb;  // K block within the chunk
+                    if (Cfg::CHUNK > 0 && kin == 0) {
+                        // a fresh accumulator for each chunk, folded by the epilogue
                         if (!mbar_wait(&acce_bar[acc], acc_phase ^ 1u, abort_flag, p.err,
                                        ERR_TIMEOUT_MMA)) {
                             ok = false;
@@ -371,17 +377,18 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                         const uint32_t koff = (uint32_t)ks * 32u;  // 32 bytes of K per MMA
                         const uint64_t da = sdesc_k128(sa + koff);
                         const uint64_t db = sdesc_k128(sb + koff);
+                        const uint32_t accum = (kin > 0 || ks > 0) ? 1u : 0u;
                         if (Cfg::MODE == MODE_FP8) {
-                            mma_f8(d, da, db, idesc, ks > 0 ? 1u : 0u);
+                            mma_f8(d, da, db, idesc, accum);
                         } else if (Cfg::MODE == MODE_BF16) {
-                            mma_f16(d, da, db, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+                            mma_f16(d, da, db, idesc, accum);
                         } else {
                             const uint32_t sa2 = sb + Cfg::B_BYTES;   // A lo
                             const uint32_t sb2 = sa2 + Cfg::A_BYTES;  // B lo
                             const uint64_t da2 = sdesc_k128(sa2 + koff);
                             const uint64_t db2 = sdesc_k128(sb2 + koff);
                             // small terms first: lo*hi, hi*lo, then hi*hi
-                            mma_f16(d, da2, db, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+                            mma_f16(d, da2, db, idesc, accum);
                             mma_f16(d, da, db2, idesc, 1u);
                             mma_f16(d, da, db, idesc, 1u);
                         }
@@ -392,7 +399,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                         stage = 0;
                         phase ^= 1u;
                     }
-                    if (Cfg::MODE == MODE_FP8) {
+                    if (Cfg::CHUNK > 0 && (kin == Cfg::CHUNK - 1 || kb == nkb - 1)) {
                         mma_commit(&accf_bar[acc]);
                         if (++acc == 2) {
                             acc = 0;
@@ -401,7 +408,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     }
                 }
                 if (!ok) break;
-                if (Cfg::MODE != MODE_FP8) {
+                if (Cfg::CHUNK == 0) {
                     mma_commit(&accf_bar[acc]);
                     if (++acc == 2) {
                         acc = 0;
@@ -439,12 +446,13 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             float* crow = p.C + (size_t)row * p.ldc;
             const bool row_ok = row < p.M;
             const bool vec = ((p.ldc & 3) == 0) && ((((uintptr_t)p.C) & 15u) == 0);
-            if (Cfg::MODE == MODE_FP8) {
+            if (Cfg::CHUNK > 0) {
                 float accr[Cfg::BN / (Cfg::EPI_WARPS / 4)];
 #pragma unroll
                 for (int j = 0; j < ncol; ++j) accr[j] = 0.f;
                 const int ksa = (p.K + 127) / 128, nsb = (p.N + 127) / 128;
-                for (int kb = 0; kb < nkb; ++kb) {
+                const int nchunks = (nkb + Cfg::CHUNK - 1) / Cfg::CHUNK;
+                for (int ch = 0; ch < nchunks; ++ch) {
                     int w = 1;
                     if (lane == 0)
                         w = mbar_wait(&accf_bar[acc], acc_phase, abort_flag, p.err,
@@ -457,7 +465,6 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     while (!mbar_try_wait(&accf_bar[acc], acc_phase)) {
                     }
                     tc_fence_after();
-                    const float sc = __ldg(p.sA + (size_t)tm * ksa + kb) * __ldg(p.sB + (size_t)kb * nsb + tn);
 #pragma unroll
                     for (int c = 0; c < ncol / 32; ++c) {
                         uint32_t r[32];
@@ -465,9 +472,17 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                                       (uint32_t)(acc * Cfg::BN + col0 + c * 32),
                                   r);
                         tmem_ld_wait();
+                        if (Cfg::MODE == MODE_FP8) {
+                            // chunk sum times sA * sB (the tile scales of this 128-deep chunk)
+                            const float sc = __ldg(p.sA + (size_t)tm * ksa + ch) *
+                                             __ldg(p.sB + (size_t)ch * nsb + n0 / 128);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            accr[c * 32 + j] = fmaf(__uint_as_float(r[j]), sc, accr[c * 32 + j]);
+                            for (int j = 0; j < 32; ++j)
+                                accr[c * 32 + j] = fmaf(__uint_as_float(r[j]), sc, accr[c * 32 + j]);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) accr[c * 32 + j] += __uint_as_float(r[j]);
+                        }
                     }
                     tc_fence_before();
                     mbar_arrive(&acce_bar[acc]);
@@ -632,7 +647,7 @@ static const TcVariant* tc_table(int* n) {
     static const TcVariant t[] = {
         tcv<MODE_BF16, 256, 4>(PGK_FAM_TC_BF16),   tcv<MODE_BF16, 128, 6>(PGK_FAM_TC_BF16),
         tcv<MODE_SPLIT, 128, 3>(PGK_FAM_TC_SPLIT), tcv<MODE_SPLIT, 256, 2>(PGK_FAM_TC_SPLIT),
-        tcv<MODE_FP8, 128, 6>(PGK_FAM_TC_FP8),     tcv<MODE_FP8, 128, 4>(PGK_FAM_TC_FP8),
+        tcv<MODE_FP8, 128, 6>(PGK_FAM_TC_FP8),     tcv<MODE_FP8, 256, 4>(PGK_FAM_TC_FP8),
     };
     *n = (int)(sizeof(t) / sizeof(t[0]));
     return t;

@@ -92,6 +92,9 @@ _SIGS = {
     "pgk_autotune": (_i, [_i, _i, _i, _i, _p, _i, _p, _i, _p, _i, ctypes.POINTER(Params), _i, _i,
                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Params), ctypes.c_char_p, _p]),
     "pgk_default_candidates": (_i, [_i, ctypes.POINTER(Params), _i]),
+    "pgk_grouped_variants": (_i, [ctypes.POINTER(Params), _i, ctypes.POINTER(ctypes.c_int)]),
+    "pgk_autotune_grouped": (_i, [_i, ctypes.POINTER(Problem), ctypes.POINTER(Params), _i, _i,
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Params), _p]),
     "pgk_tune_cache_put": (_i, [_i, _i, _i, _i, ctypes.POINTER(Params)]),
     "pgk_tune_cache_get": (_i, [_i, _i, _i, _i, ctypes.POINTER(Params)]),
     "pgk_tune_cache_save": (_i, [ctypes.c_char_p]),
@@ -223,6 +226,25 @@ def gemm_grouped(problems, dtype=F32, prog: Params | None = None, use_graph=0, b
                                 ctypes.byref(prog) if prog is not None else None, int(use_graph),
                                 int(beta), _stream(stream))
     _check(st, "pgk_gemm_grouped")
+
+
+def grouped_variants() -> list:
+    n = ctypes.c_int(0)
+    lib().pgk_grouped_variants(None, 0, ctypes.byref(n))
+    arr = (Params * n.value)()
+    lib().pgk_grouped_variants(arr, n.value, None)
+    return [arr[i] for i in range(n.value)]
+
+
+def autotune_grouped(problems, candidates=None, reps=3, stream=None):
+    """Returns (best Params, list of (Params, ms))."""
+    cand = candidates if candidates is not None else grouped_variants()
+    arr = (Params * len(cand))(*cand)
+    ms = (ctypes.c_float * len(cand))()
+    best = Params()
+    _check(lib().pgk_autotune_grouped(len(problems), problems, arr, len(cand), reps, ms,
+                                      ctypes.byref(best), _stream(stream)), "pgk_autotune_grouped")
+    return best, [(cand[i], ms[i]) for i in range(len(cand))]
 
 
 # --------------------------------------------------------- low precision
