@@ -188,6 +188,7 @@ def main():
     ap.add_argument("--size", type=int, default=8192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune-log", default=None, help="append the autotuner's CSV rows here")
     ap.add_argument("--params", default=None,
                     help="B0,B1,s,sr,tile: use these program parameters instead of autotuning")
     args = ap.parse_args()
@@ -223,7 +224,8 @@ def main():
     for f in forms:
         try:
             fixed = pgk.params(*[int(x) for x in args.params.split(",")]) if args.params else None
-            prog, err = prepare_form(f, Ad, Bd, C, A, B, stream, pgk, torch, np, fixed)
+            prog, err = prepare_form(f, Ad, Bd, C, A, B, stream, pgk, torch, np, fixed,
+                                     args.tune_log)
             if err <= FORM_TOL[f]:
                 form = f
                 break
@@ -297,7 +299,7 @@ def main():
     return 0
 
 
-def prepare_form(form, Ad, Bd, C, A, B, stream, pgk, torch, np, fixed=None):
+def prepare_form(form, Ad, Bd, C, A, B, stream, pgk, torch, np, fixed=None, tune_log=None):
     """Autotune the form's program parameters on the real operands and measure
     its relative Frobenius error on 64 sampled rows against the FP64 oracle."""
     import oracle
@@ -310,7 +312,8 @@ def prepare_form(form, Ad, Bd, C, A, B, stream, pgk, torch, np, fixed=None):
         if fixed is not None:
             best = fixed
         else:
-            best, _ = pgk.autotune(Ad, Bd, C, dt, candidates=cands, reps=2, stream=stream)
+            best, _ = pgk.autotune(Ad, Bd, C, dt, candidates=cands, reps=2, stream=stream,
+                                   log_path=tune_log)
         pgk.gemm(Ad, Bd, C, dt, best, stream=stream)
     torch.cuda.synchronize()
     M = A.shape[0]

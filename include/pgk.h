@@ -266,17 +266,19 @@ PGK_API pgk_status pgk_relerr(int rows, int cols, const float* C, int ldc, const
 
 /* Number of parameters of the 7 -> 64 -> 64 -> 1 ReLU network, packed as
  * W1 (64x7 row-major), b1 (64), W2 (64x64 row-major), b2 (64), w3 (64), b3. */
-#define PGK_MLP_PARAMS 4673
+#define PGK_MLP_PARAMS 4737
 
 /* y[n] = MLP(X[n][7]) for n samples (device FP32).  Errors: INVALID_ARG, CUDA. */
 PGK_API pgk_status pgk_mlp_forward(int n, const float* X, const float* theta, float* y, void* stream);
 
-/* Mean squared error of the n samples and its gradient w.r.t. theta:
+/* Mean squared error of n samples and its gradient w.r.t. theta:
  * loss[0] = (1/n) sum (y - t)^2 and grad[PGK_MLP_PARAMS] (device FP32,
- * overwritten).  Deterministic (fixed reduction order).  n <= 65536.
+ * overwritten).  Sample r is row idx[r] of X / entry idx[r] of t (idx: device
+ * int array of n entries, e.g. a minibatch of a shuffled epoch), or row r when
+ * idx is NULL.  Deterministic (fixed reduction order).  n <= 65536.
  * Errors: INVALID_ARG, CUDA. */
-PGK_API pgk_status pgk_mlp_loss_grad(int n, const float* X, const float* t, const float* theta,
-                             float* grad, float* loss, void* stream);
+PGK_API pgk_status pgk_mlp_loss_grad(int n, const int* idx, const float* X, const float* t,
+                                     const float* theta, float* grad, float* loss, void* stream);
 
 /* One Adam step (step counts from 1) on `count` parameters in place (device).
  * Errors: INVALID_ARG, CUDA. */

@@ -14,7 +14,7 @@ theta <- theta - lr * mhat / (sqrt(vhat) + eps), mhat = m/(1-b1^t),
 vhat = v/(1-b2^t)).  relu'(z) is taken as 1 for z > 0 and 0 otherwise.
 
 Parameters travel as one flat vector in the order W1 (64x7 row-major), b1 (64),
-W2 (64x64 row-major), b2 (64), w3 (64), b3 (1): 4673 values.
+W2 (64x64 row-major), b2 (64), w3 (64), b3 (1): 4737 values.
 """
 from __future__ import annotations
 

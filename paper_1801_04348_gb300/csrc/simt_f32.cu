@@ -203,6 +203,9 @@ void register_simt_variants(std::vector<Variant>& v) {
     add_rb<32, 16, 4, 8, 8>(v);
     add_rb<16, 32, 8, 8, 8>(v);
     add_rb<32, 16, 8, 8, 8>(v);
+    add_rb<16, 16, 8, 8, 32>(v);
+    add_rb<16, 16, 8, 16, 8>(v);
+    add_rb<16, 16, 16, 8, 8>(v);
 }
 
 }  // namespace pgk

@@ -25,7 +25,7 @@ struct RbCfg {
     static constexpr int SMEM = 2 * (A_ELEMS + B_ELEMS) * 4;   // = 8 BK (BM + BN + 8)
     static constexpr int NA4 = BM * BK / 4, NB4 = BK * BN / 4;
     static constexpr int LA = (NA4 + NT - 1) / NT, LB = (NB4 + NT - 1) / NT;
-    static constexpr int MINB = NT <= 128 ? 4 : (NT <= 256 ? 2 : 1);
+    static constexpr int MINB = SR * S > 64 ? 1 : (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1));
     static_assert(SR % 4 == 0 && S % 4 == 0 && BK % 4 == 0, "micro tile in float4 groups");
 };
 

@@ -22,7 +22,7 @@ DTYPES = {"f32": F32, "bf16": BF16, "fp8": FP8_E4M3, "split": SPLIT_BF16}
 LEAF_4A3A, LEAF_3B4A, LEAF_3B4B = 0, 1, 2
 FAM_PAPER, FAM_RB, FAM_DIRECT, FAM_TC_BF16, FAM_TC_SPLIT, FAM_TC_FP8 = range(6)
 REG_CLASSES = 11
-MLP_PARAMS = 4673
+MLP_PARAMS = 4737
 
 
 class PgkError(RuntimeError):
@@ -87,7 +87,7 @@ _SIGS = {
                            ctypes.POINTER(Params), _p]),
     "pgk_relerr": (_i, [_i, _i, _p, _i, _p, _i, _p, _p, _p]),
     "pgk_mlp_forward": (_i, [_i, _p, _p, _p, _p]),
-    "pgk_mlp_loss_grad": (_i, [_i, _p, _p, _p, _p, _p, _p]),
+    "pgk_mlp_loss_grad": (_i, [_i, _p, _p, _p, _p, _p, _p, _p]),
     "pgk_mlp_adam": (_i, [_i, _p, _p, _p, _p, _i, _f, _f, _f, _f, _p]),
     "pgk_autotune": (_i, [_i, _i, _i, _i, _p, _i, _p, _i, _p, _i, ctypes.POINTER(Params), _i, _i,
                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Params), ctypes.c_char_p, _p]),
@@ -290,8 +290,9 @@ def mlp_forward(X, theta, y, stream=None):
            "pgk_mlp_forward")
 
 
-def mlp_loss_grad(X, t, theta, grad, loss, stream=None):
-    _check(lib().pgk_mlp_loss_grad(X.shape[0], _ptr(X), _ptr(t), _ptr(theta), _ptr(grad), _ptr(loss),
+def mlp_loss_grad(X, t, theta, grad, loss, idx=None, stream=None, n=None):
+    n = (idx.shape[0] if idx is not None else X.shape[0]) if n is None else n
+    _check(lib().pgk_mlp_loss_grad(n, _ptr(idx), _ptr(X), _ptr(t), _ptr(theta), _ptr(grad), _ptr(loss),
                                    _stream(stream)), "pgk_mlp_loss_grad")
 
 
