@@ -65,7 +65,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -181,7 +181,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (0 = as many as fill about 3 s)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="auto", choices=["auto", "f32", "split", "bf16", "fp8"])
@@ -236,15 +237,31 @@ def main():
 
     step, gemm_events, launches_per_step, alg = make_step(form, prog, Ad, Bd, C, M, N, K, sh, pgk,
                                                           torch, dev)
+    if args.steps <= 0:
+        with torch.cuda.stream(stream):
+            step()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            step()
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+        args.steps = int(min(2000, max(10, 3.0 / max(dt, 1e-6))))
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
     torch.cuda.synchronize(dev)
-    if ws > 1:
-        torch.distributed.barrier()
+    # nvidia-smi needs a moment to start: keep the GPU busy with extra untimed
+    # steps for ~0.6 s after starting it, so the samples see the kernel under load
     sampler = ClockSampler(local)
     sampler.start()
-    time.sleep(0.3)
+    t_busy = time.perf_counter()
+    with torch.cuda.stream(stream):
+        while time.perf_counter() - t_busy < 0.6:
+            step()
+            torch.cuda.synchronize(dev)
+    gemm_events.clear()
+    if ws > 1:
+        torch.distributed.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
@@ -273,7 +290,8 @@ def main():
         e2e = measure_e2e(form, prog, A, B, M, N, K, dev, stream, pgk, torch, args, ws)
 
     pk, pk_src = peaks()
-    roof = roofline(form, alg, gemm_ms, ms / args.steps, machine, pk, pk_src, clocks)
+    roof = roofline(form, alg, gemm_ms, ms / args.steps, machine, pk, pk_src, clocks,
+                    recorded_traffic(form, prog) if M == 8192 else None)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(M, N, K, seed=0)
@@ -386,14 +404,46 @@ def make_step(form, prog, Ad, Bd, C, M, N, K, sh, pgk, torch, dev):
     return step, events, 3, {"flops": 2.0 * M * N * K}
 
 
-def roofline(form, alg, gemm_ms, step_ms, machine, pk, pk_src, clocks):
+KERNEL_SOURCES = {"f32": ["simt_rb.cuh", "simt_f32.cu"], "split": ["tc_gemm.cu"],
+                  "bf16": ["tc_gemm.cu"], "fp8": ["tc_gemm.cu"]}
+
+
+def recorded_traffic(form, prog):
+    """DRAM bytes per GEMM launch from the committed ncu summary
+    profiles/traffic_<form>.txt, or None when that summary is missing, was taken
+    for other program parameters, or the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_{form}.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as f:
+        for line in f:
+            parts = line.split(None, 1)
+            if len(parts) == 2:
+                rec[parts[0]] = parts[1].strip()
+    h = hashlib.sha1()
+    for src in KERNEL_SOURCES[form]:
+        with open(os.path.join(ROOT, "paper_1801_04348_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    if rec.get("source_sha1") != h.hexdigest():
+        return None
+    if rec.get("program_params") != ",".join(str(x) for x in prog.as_tuple()):
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def roofline(form, alg, gemm_ms, step_ms, machine, pk, pk_src, clocks, traffic=None):
     kern_ms = statistics.mean(gemm_ms) if gemm_ms else step_ms
     achieved = alg["flops"] / (kern_ms * 1e-3) / 1e12
     if form == "f32":
         f = pk.get("sm_max_mhz", 2070.0)
         peak = machine.sm_count * 128 * 2 * f * 1e6 / 1e12
         out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-               "frac": achieved / peak, "traffic": None,
+               "frac": achieved / peak, "traffic": traffic,
                "kernel": "k_rb (register-blocked FP32 SIMT)",
                "peak_source": f"{machine.sm_count} SMs x 128 FP32 lanes x 2 flop x {f:.0f} MHz "
                               f"(max SM clock, {pk_src})"}
@@ -407,7 +457,7 @@ def roofline(form, alg, gemm_ms, step_ms, machine, pk, pk_src, clocks):
         peak = pk["bf16_tflops"]
         src = f"bf16 burst ({pk_src})"
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "k_tc_gemm (tcgen05)",
+            "frac": achieved / peak, "traffic": traffic, "kernel": "k_tc_gemm (tcgen05)",
             "peak_source": src, "flops_per_launch": alg["flops"]}
 
 
