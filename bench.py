@@ -274,15 +274,8 @@ def main():
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     gemm_ms = [a.elapsed_time(b) for a, b in gemm_events[-args.steps:]] if gemm_events else []
-    t_local = ms / 1e3
-    if ws > 1:
-        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    flops = 2.0 * M * N * K * args.steps * ws
-    value = flops / t_max / 1e12
+    t_max = max_over_ranks(ms / 1e3, dev, ws)
+    value = whole_job_tflops(2.0 * M * N * K * args.steps, t_max, ws)
 
     # end to end: host (pinned) inputs -> device -> GEMM -> host result
     e2e = None
@@ -315,6 +308,24 @@ def main():
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def max_over_ranks(t_local, device, ws):
+    """Slowest rank's time (seconds): every rank ran the same number of steps
+    between the same barriers, so the job takes as long as its slowest rank."""
+    if ws <= 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(flops_per_rank, t_max, ws):
+    """Weak scaling: each rank does its own GEMMs; whole-job rate = all ranks'
+    flops over the slowest rank's time."""
+    return flops_per_rank * ws / t_max / 1e12
 
 
 def prepare_form(form, Ad, Bd, C, A, B, stream, pgk, torch, np, fixed=None, tune_log=None):
