@@ -280,6 +280,29 @@ PGK_API pgk_status pgk_mlp_forward(int n, const float* X, const float* theta, fl
 PGK_API pgk_status pgk_mlp_loss_grad(int n, const int* idx, const float* X, const float* t,
                                      const float* theta, float* grad, float* loss, void* stream);
 
+/* Largest sample count accepted by pgk_mlp_loss_grad_noalloc. */
+#define PGK_MLP_NOALLOC_MAX_SAMPLES 2048
+
+/* Same result as pgk_mlp_loss_grad, but the call allocates no memory: no
+ * cudaMalloc, cudaFree or allocating library routine.  This serves callers
+ * that cannot allocate device memory where they need a gradient (work being
+ * captured into a CUDA graph, real-time loops that forbid allocation after
+ * start-up, hosts whose device memory belongs to their own pool).  The paper
+ * has no counterpart to this entry point.  The per-tile partial gradients live
+ * in one static device array of PGK_MLP_NOALLOC_MAX_SAMPLES / 16 tiles
+ * (about 2.4 MB), which every GPU that loads the library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (once per device, with the device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents; every slot a call reads it first writes, so nothing needs
+ * clearing.  Calls that overlap on the GPU (different streams, or different
+ * host threads) race on the array: serialise them.  Arguments as
+ * pgk_mlp_loss_grad.  Errors: INVALID_ARG (n < 1, n > the limit, NULL
+ * pointers), CUDA. */
+PGK_API pgk_status pgk_mlp_loss_grad_noalloc(int n, const int* idx, const float* X,
+                                             const float* t, const float* theta, float* grad,
+                                             float* loss, void* stream);
+
 /* One Adam step (step counts from 1) on `count` parameters in place (device).
  * Errors: INVALID_ARG, CUDA. */
 PGK_API pgk_status pgk_mlp_adam(int count, float* theta, const float* grad, float* m, float* v,

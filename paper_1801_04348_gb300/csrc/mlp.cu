@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "pgk_internal.cuh"
 
@@ -249,3 +250,62 @@ pgk_status pgk_mlp_adam(int count, float* theta, const float* grad, float* m, fl
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ allocation-free gradient
+// Some callers cannot allocate device memory at the point where they need a
+// gradient: code that runs while a CUDA graph is being captured, real-time or
+// embedded loops that forbid allocation after start-up, and hosts whose memory
+// is owned by their own pool allocator.  For them the per-tile partials live
+// in a file-scope device array sized for PGK_MLP_NOALLOC_MAX_SAMPLES samples.
+// Every GPU that loads the library holds this array until the process exits.
+namespace pgk {
+static constexpr int NOALLOC_TILES = PGK_MLP_NOALLOC_MAX_SAMPLES / TILE;
+static __device__ __align__(256) float g_mlp_noalloc_partial[NOALLOC_TILES * (NPARAM + 1)];
+
+static std::mutex g_noalloc_mu;
+static float* g_noalloc_ptr[64];  // device address of the array, per device
+
+// In host code the array's name is only a host-side stand-in, so its device
+// address is looked up once per device (with that device current) and cached.
+static pgk_status noalloc_scratch(float** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) {
+        set_error("device index %d out of range", dev);
+        return PGK_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_mlp_noalloc_partial);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the gradient scratch");
+        g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return PGK_OK;
+}
+}  // namespace pgk
+
+extern "C" pgk_status pgk_mlp_loss_grad_noalloc(int n, const int* idx, const float* X,
+                                                const float* t, const float* theta, float* grad,
+                                                float* loss, void* stream) {
+    if (n < 1 || !X || !t || !theta || !grad || !loss) {
+        set_error("bad MLP gradient arguments");
+        return PGK_ERR_INVALID_ARG;
+    }
+    if (n > PGK_MLP_NOALLOC_MAX_SAMPLES) {
+        set_error("pgk_mlp_loss_grad_noalloc: %d samples exceed the static scratch limit of %d "
+                  "(use pgk_mlp_loss_grad or split the batch)", n, PGK_MLP_NOALLOC_MAX_SAMPLES);
+        return PGK_ERR_INVALID_ARG;
+    }
+    float* partial = nullptr;
+    pgk_status st = noalloc_scratch(&partial);
+    if (st != PGK_OK) return st;
+    const int tiles = (n + TILE - 1) / TILE;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_mlp_grad_tile<<<tiles, GTHREADS, 0, s>>>(n, idx, X, t, theta, partial);
+    k_mlp_grad_reduce<<<(NPARAM + 1 + 255) / 256, 256, 0, s>>>(tiles, n, partial, grad, loss);
+    PGK_CUDA_TRY(cudaGetLastError(), "MLP gradient launch");
+    return PGK_OK;
+}

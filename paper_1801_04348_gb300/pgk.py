@@ -88,6 +88,7 @@ _SIGS = {
     "pgk_relerr": (_i, [_i, _i, _p, _i, _p, _i, _p, _p, _p]),
     "pgk_mlp_forward": (_i, [_i, _p, _p, _p, _p]),
     "pgk_mlp_loss_grad": (_i, [_i, _p, _p, _p, _p, _p, _p, _p]),
+    "pgk_mlp_loss_grad_noalloc": (_i, [_i, _p, _p, _p, _p, _p, _p, _p]),
     "pgk_mlp_adam": (_i, [_i, _p, _p, _p, _p, _i, _f, _f, _f, _f, _p]),
     "pgk_autotune": (_i, [_i, _i, _i, _i, _p, _i, _p, _i, _p, _i, ctypes.POINTER(Params), _i, _i,
                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Params), ctypes.c_char_p, _p]),
@@ -294,6 +295,14 @@ def mlp_loss_grad(X, t, theta, grad, loss, idx=None, stream=None, n=None):
     n = (idx.shape[0] if idx is not None else X.shape[0]) if n is None else n
     _check(lib().pgk_mlp_loss_grad(n, _ptr(idx), _ptr(X), _ptr(t), _ptr(theta), _ptr(grad), _ptr(loss),
                                    _stream(stream)), "pgk_mlp_loss_grad")
+
+
+def mlp_loss_grad_noalloc(X, t, theta, grad, loss, idx=None, stream=None, n=None):
+    """pgk_mlp_loss_grad_noalloc: the gradient without any device allocation
+    (static scratch, at most 2048 samples per call)."""
+    n = (idx.shape[0] if idx is not None else X.shape[0]) if n is None else n
+    _check(lib().pgk_mlp_loss_grad_noalloc(n, _ptr(idx), _ptr(X), _ptr(t), _ptr(theta), _ptr(grad),
+                                           _ptr(loss), _stream(stream)), "pgk_mlp_loss_grad_noalloc")
 
 
 def mlp_adam(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
