@@ -69,27 +69,63 @@ __global__ void k_cvt_rows(int rows, int cols, const float* __restrict__ src, in
     }
 }
 
-// Transposed conversion through a 32 x 32 shared tile: reads are coalesced
-// along src rows, writes along dst rows (= src columns).
+// Transposed conversion through a 64 x 64 shared tile: src rows are read as
+// float4 (coalesced along src rows), each dst row (a src column) is written as
+// 32-bit pairs of BF16 values (a full 128-byte segment per warp).
 template <int MODE>
-__global__ void k_cvt_transpose(int rows, int cols, const float* __restrict__ src, int lds,
-                                uint16_t* __restrict__ d0, uint16_t* __restrict__ d1, int ldd) {
-    __shared__ uint16_t th[32][33];
-    __shared__ uint16_t tl[32][33];
-    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int r = r0 + y, c = c0 + threadIdx.x;
-        uint16_t h = 0, l = 0;
-        if (r < rows && c < cols) convert_one<MODE>(__ldg(src + (size_t)r * lds + c), h, l);
-        th[y][threadIdx.x] = h;
-        if (MODE == 1) tl[y][threadIdx.x] = l;
+__global__ void __launch_bounds__(256) k_cvt_transpose(int rows, int cols,
+                                                       const float* __restrict__ src, int lds,
+                                                       uint16_t* __restrict__ d0,
+                                                       uint16_t* __restrict__ d1, int ldd,
+                                                       int vec_in, int pair_out) {
+    __shared__ float t[64][65];
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int idx = tid + i * 256;
+        const int r = idx >> 4, c = (idx & 15) * 4;
+        const int gr = r0 + r, gc = c0 + c;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (gr < rows) {
+            const float* sp = src + (size_t)gr * lds + gc;
+            if (vec_in && gc + 3 < cols) {
+                const float4 f = __ldg(reinterpret_cast<const float4*>(sp));
+                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (gc + u < cols) v[u] = __ldg(sp + u);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[r][c + u] = v[u];
     }
     __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int c = c0 + y, r = r0 + threadIdx.x;  // dst row c, dst col r
-        if (c < cols && r < rows) {
-            d0[(size_t)c * ldd + r] = th[threadIdx.x][y];
-            if (MODE == 1) d1[(size_t)c * ldd + r] = tl[threadIdx.x][y];
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = warp * 8 + j;           // dst row c0 + c
+        const int gc = c0 + c;
+        if (gc >= cols) break;
+        const int gr = r0 + 2 * lane;         // dst columns gr, gr + 1
+        uint16_t h0, l0, h1, l1;
+        convert_one<MODE>(t[2 * lane][c], h0, l0);
+        convert_one<MODE>(t[2 * lane + 1][c], h1, l1);
+        uint16_t* o0 = d0 + (size_t)gc * ldd + gr;
+        uint16_t* o1 = MODE == 1 ? d1 + (size_t)gc * ldd + gr : nullptr;
+        if (pair_out && gr + 1 < rows) {
+            *reinterpret_cast<uint32_t*>(o0) = h0 | ((uint32_t)h1 << 16);
+            if (MODE == 1) *reinterpret_cast<uint32_t*>(o1) = l0 | ((uint32_t)l1 << 16);
+        } else {
+            if (gr < rows) {
+                o0[0] = h0;
+                if (MODE == 1) o1[0] = l0;
+            }
+            if (gr + 1 < rows) {
+                o0[1] = h1;
+                if (MODE == 1) o1[1] = l1;
+            }
         }
     }
 }
@@ -161,12 +197,15 @@ template <int MODE>
 static pgk_status launch_cvt(int rows, int cols, const float* src, int lds, uint16_t* d0,
                              uint16_t* d1, int ldd, int transpose, cudaStream_t st) {
     if (transpose) {
-        dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+        dim3 grid((cols + 63) / 64, (rows + 63) / 64);
         if (grid.y > 65535) {
             set_error("too many rows for the transposing conversion");
             return PGK_ERR_INVALID_ARG;
         }
-        k_cvt_transpose<MODE><<<grid, block, 0, st>>>(rows, cols, src, lds, d0, d1, ldd);
+        const int vec_in = aligned(src, 16) && lds % 4 == 0;
+        const int pair_out = aligned(d0, 4) && ldd % 2 == 0 && (MODE == 0 || aligned(d1, 4));
+        k_cvt_transpose<MODE><<<grid, 256, 0, st>>>(rows, cols, src, lds, d0, d1, ldd, vec_in,
+                                                    pair_out);
     } else {
         const int vec = aligned(src, 16) && lds % 4 == 0 && aligned(d0, 8) && ldd % 4 == 0 &&
                         (MODE == 0 || aligned(d1, 8));

@@ -1,0 +1,240 @@
+"""Measurements of the GEMM workloads beside the headline benchmark.
+
+    python -m paper_1801_04348_gb300.experiments --out DIR [config1 scale grouped precision]
+
+config1    M = N = K = 256, uniform[-1,1] seed 0: every (B0, B1, s) of {8,16,32}^2 x {1,2,4};
+           case leaf, registers, time, and relative error against the FP64 oracle.
+scale      FP32 at 4096^3, 8192^3, 8192 x 1024 x 4096, 16384 x 64 x 16384: full autotune
+           sweep of the register-blocked variants, best time, TFLOP/s, fraction of the SIMT
+           peak (152 SMs x 128 lanes x 2 flop x 2070 MHz), and GB/s of compulsory traffic.
+grouped    512 FP32 GEMMs, M, N, K log-uniform in [32, 2048] (multiples of 16, seed 0),
+           normal(0,1) operands: one grouped persistent launch (eager and CUDA-graph
+           replay, tile variant from pgk_autotune_grouped) against 512 separate pgk_gemm
+           launches (eager and captured in one CUDA graph).
+precision  8192^3, normal(0,1) and row-scaled by 10^uniform(-3,3): every form's step
+           time (FP32 in/out, preparation included), kernel time on prepared operands,
+           and relative Frobenius error on 64 sampled rows against the FP64 oracle.
+
+Timing: CUDA events on the launching stream after warm-up; medians of repeated runs.
+The oracle is only used for the error columns (test infrastructure).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import time
+
+import numpy as np
+
+from . import inputs, pgk
+
+PEAK_MHZ = 2070.0
+
+
+def _events_ms(fn, reps, stream):
+    import torch
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def _rel_err_rows(Cd, A, B, rows):
+    import torch
+
+    import oracle
+    ref = oracle.gemm(A, B, rows=rows)
+    got = Cd[torch.from_numpy(rows).to(Cd.device)].cpu().numpy()
+    return oracle.rel_frobenius(got, ref)
+
+
+def simt_peak(machine):
+    return machine.sm_count * 128 * 2 * PEAK_MHZ * 1e6 / 1e12
+
+
+def config1(dev, stream):
+    import torch
+    M = N = K = 256
+    A, B = inputs.gemm_operands(M, N, K, seed=0)
+    Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    C = torch.empty(M, N, device=dev)
+    m = pgk.machine_query(dev.index or 0)
+    rows = np.arange(M, dtype=np.int64)
+    out = []
+    for b0 in (8, 16, 32):
+        for b1 in (8, 16, 32):
+            for s in (1, 2, 4):
+                p = pgk.params(b0, b1, s)
+                st, c = pgk.select_case(m, M, N, K, pgk.F32, p, raise_on_error=False)
+                rec = {"B0": b0, "B1": b1, "s": s, "status": pgk.STATUS[st]}
+                if st == 0:
+                    run = lambda: pgk.gemm(Ad, Bd, C, pgk.F32, p, stream=stream)
+                    run()
+                    ms = _events_ms(run, 20, stream)
+                    rec.update(leaf=c.leaf, regs=c.regs, smem=c.smem_bytes, ms=ms,
+                               tflops=2.0 * M * N * K / ms / 1e9,
+                               rel_err=_rel_err_rows(C, A, B, rows))
+                out.append(rec)
+    return {"config": "config1 256^3 paper-form grid", "points": out,
+            "feasible": sum(1 for r in out if r["status"] == "PGK_OK")}
+
+
+def scale(dev, stream):
+    import torch
+    m = pgk.machine_query(dev.index or 0)
+    peak = simt_peak(m)
+    res = []
+    cands = [p for p in pgk.default_candidates(pgk.F32) if p.sr > 1]
+    for (M, N, K) in [(4096, 4096, 4096), (8192, 8192, 8192), (8192, 1024, 4096), (16384, 64, 16384)]:
+        A, B = inputs.gemm_operands(M, N, K, seed=0)
+        Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        C = torch.empty(M, N, device=dev)
+        best, table = pgk.autotune(Ad, Bd, C, pgk.F32, candidates=cands, reps=3, stream=stream)
+        run = lambda: pgk.gemm(Ad, Bd, C, pgk.F32, best, stream=stream)
+        ms = _events_ms(run, 5, stream)
+        rows = np.linspace(0, M - 1, 32).astype(np.int64)
+        fl = 2.0 * M * N * K
+        byt = 4.0 * (M * K + K * N + M * N)
+        res.append({"M": M, "N": N, "K": K, "best": list(best.as_tuple()), "ms": ms,
+                    "tflops": fl / ms / 1e9, "simt_peak_tflops": peak,
+                    "frac_of_simt_peak": fl / ms / 1e9 / peak, "gbs": byt / ms / 1e6,
+                    "rel_err_32_rows": _rel_err_rows(C, A, B, rows),
+                    "sweep": [(list(p.as_tuple()), t) for p, t in table]})
+        del Ad, Bd, C
+        torch.cuda.empty_cache()
+    return {"config": "scale FP32 tuned", "shapes": res}
+
+
+def grouped(dev, stream):
+    import torch
+    dims = inputs.log_uniform_dims(512, 0, 32, 2048, 16)
+    trip = []
+    for i, (M, N, K) in enumerate(dims):
+        A, B = inputs.gemm_operands(int(M), int(N), int(K), seed=1 + 2 * i, dist="normal")
+        trip.append((torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev),
+                     torch.empty(int(M), int(N), device=dev)))
+    flops = float(sum(2.0 * int(M) * int(N) * int(K) for M, N, K in dims))
+    probs = pgk.make_problems(trip)
+    best, table = pgk.autotune_grouped(probs, reps=3, stream=stream)
+    sh = stream.cuda_stream
+    eager = lambda: pgk.gemm_grouped(probs, pgk.F32, best, stream=sh)
+    graph = lambda: pgk.gemm_grouped(probs, pgk.F32, best, use_graph=1, stream=sh)
+    eager()
+    graph()
+    t_grouped = _events_ms(eager, 10, stream)
+    t_grouped_graph = _events_ms(graph, 10, stream)
+
+    def separate():
+        for A, B, C in trip:
+            pgk.gemm(A, B, C, pgk.F32, None, stream=sh)
+    separate()
+    t_sep = _events_ms(separate, 5, stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        separate()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+            separate()
+    replay = lambda: g.replay()
+    replay()
+    t_sep_graph = _events_ms(replay, 10, stream)
+    return {"config": "grouped 512 GEMMs", "flops": flops, "tile_variant": list(best.as_tuple()),
+            "variant_sweep_ms": [(list(p.as_tuple()), t) for p, t in table],
+            "grouped_ms": t_grouped, "grouped_graph_ms": t_grouped_graph,
+            "separate_ms": t_sep, "separate_graph_ms": t_sep_graph,
+            "tflops": {"grouped": flops / t_grouped / 1e9,
+                       "grouped_graph": flops / t_grouped_graph / 1e9,
+                       "separate": flops / t_sep / 1e9,
+                       "separate_graph": flops / t_sep_graph / 1e9}}
+
+
+def precision(dev, stream):
+    import torch
+    M = N = K = 8192
+    sh = stream.cuda_stream
+    out = []
+    for dist in ("normal", "normal_rowscaled"):
+        A, B = inputs.gemm_operands(M, N, K, seed=0, dist=dist)
+        Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        C = torch.empty(M, N, device=dev)
+        rows = np.linspace(0, M - 1, 64).astype(np.int64)
+        for name, dt in (("f32", pgk.F32), ("bf16", pgk.BF16), ("split", pgk.SPLIT_BF16),
+                         ("fp8", pgk.FP8_E4M3)):
+            cands = [p for p in pgk.default_candidates(dt) if dt != pgk.F32 or p.sr > 1]
+            best, _ = pgk.autotune(Ad, Bd, C, dt, candidates=cands, reps=2, stream=stream)
+            run = lambda: pgk.gemm(Ad, Bd, C, dt, best, stream=sh)
+            run()
+            step_ms = _events_ms(run, 10, stream)
+            err = _rel_err_rows(C, A, B, rows)
+            kern_ms = step_ms
+            pipe = 2.0
+            if dt != pgk.F32:
+                Kp = (K + 15) // 16 * 16
+                if dt == pgk.FP8_E4M3:
+                    a = torch.empty(M, Kp, dtype=torch.uint8, device=dev)
+                    b = torch.empty(N, Kp, dtype=torch.uint8, device=dev)
+                    sa = torch.empty(M // 128, K // 128, device=dev)
+                    sb = torch.empty(K // 128, N // 128, device=dev)
+                    pgk.quant_fp8(Ad, a, sa, 0, stream=sh)
+                    pgk.quant_fp8(Bd, b, sb, 1, stream=sh)
+                    k = lambda: pgk.gemm_lowp(M, N, K, dt, a, Kp, b, Kp, C, N, scaleA=sa, scaleB=sb,
+                                              prog=best, stream=sh)
+                elif dt == pgk.BF16:
+                    a = torch.empty(M, Kp, dtype=torch.int16, device=dev)
+                    b = torch.empty(N, Kp, dtype=torch.int16, device=dev)
+                    pgk.cvt_bf16(Ad, a, 0, stream=sh)
+                    pgk.cvt_bf16(Bd, b, 1, stream=sh)
+                    k = lambda: pgk.gemm_lowp(M, N, K, dt, a, Kp, b, Kp, C, N, prog=best, stream=sh)
+                else:
+                    pipe = 6.0
+                    a = torch.empty(M, Kp, dtype=torch.int16, device=dev)
+                    al = torch.empty_like(a)
+                    b = torch.empty(N, Kp, dtype=torch.int16, device=dev)
+                    bl = torch.empty_like(b)
+                    pgk.split_bf16(Ad, a, al, 0, stream=sh)
+                    pgk.split_bf16(Bd, b, bl, 1, stream=sh)
+                    k = lambda: pgk.gemm_lowp(M, N, K, dt, a, Kp, b, Kp, C, N, A_lo=al, Bt_lo=bl,
+                                              prog=best, stream=sh)
+                k()
+                kern_ms = _events_ms(k, 10, stream)
+            fl = 2.0 * M * N * K
+            out.append({"dist": dist, "form": name, "params": list(best.as_tuple()),
+                        "step_ms": step_ms, "step_tflops": fl / step_ms / 1e9,
+                        "kernel_ms": kern_ms, "kernel_pipe_tflops": pipe / 2 * fl / kern_ms / 1e9,
+                        "rel_err_64_rows": err})
+        del Ad, Bd, C
+        torch.cuda.empty_cache()
+    return {"config": "precision 8192^3", "results": out}
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("which", nargs="*", default=["config1", "scale", "grouped", "precision"])
+    args = ap.parse_args()
+    os.makedirs(args.out, exist_ok=True)
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    fns = {"config1": config1, "scale": scale, "grouped": grouped, "precision": precision}
+    for w in args.which:
+        t0 = time.time()
+        with torch.cuda.stream(stream):
+            r = fns[w](dev, stream)
+        r["wall_s"] = time.time() - t0
+        with open(os.path.join(args.out, f"{w}.json"), "w") as f:
+            json.dump(r, f)
+        print(w, json.dumps(r)[:1500], flush=True)
+
+
+if __name__ == "__main__":
+    main()
