@@ -206,6 +206,8 @@ void register_simt_variants(std::vector<Variant>& v) {
     add_rb<16, 16, 8, 8, 32>(v);
     add_rb<16, 16, 8, 16, 8>(v);
     add_rb<16, 16, 16, 8, 8>(v);
+    add_rb<16, 16, 16, 8, 16>(v);
+    add_rb<16, 16, 8, 16, 16>(v);
 }
 
 }  // namespace pgk

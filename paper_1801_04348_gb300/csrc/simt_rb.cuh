@@ -29,6 +29,20 @@ struct RbCfg {
     static_assert(SR % 4 == 0 && S % 4 == 0 && BK % 4 == 0, "micro tile in float4 groups");
 };
 
+// Blackwell's paired FP32 FMA: two IEEE fused multiply-adds (the same rounding
+// as fmaf) in one instruction on a 64-bit register pair, which halves the
+// issue slots the contraction needs.
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void fma2(uint64_t& c, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ float lo32(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi32(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+
 // Blocks visit tiles in groups of 8 tile-rows so that concurrently resident
 // blocks share panels of A and B in L2.
 __device__ __forceinline__ void grouped_tile_coords(int pid, int tiles_m, int tiles_n, int& bm,
@@ -135,11 +149,12 @@ struct RbTile {
         const int t0 = tid / Cfg::B1, t1 = tid % Cfg::B1;
         float* As = smem;
         float* Bs = smem + 2 * Cfg::A_ELEMS;
-        float acc[Cfg::SR][Cfg::S];
+        // acc2[i][2 ww + h] holds the outputs of row i, columns 4 ww + 2 h and 4 ww + 2 h + 1
+        uint64_t acc2[Cfg::SR][Cfg::S / 2];
 #pragma unroll
         for (int i = 0; i < Cfg::SR; ++i)
 #pragma unroll
-            for (int j = 0; j < Cfg::S; ++j) acc[i][j] = 0.f;
+            for (int j = 0; j < Cfg::S / 2; ++j) acc2[i][j] = 0ull;
 
         const int nk = (K + Cfg::BK - 1) / Cfg::BK;
         float4 ra[Cfg::LA], rb[Cfg::LB];
@@ -158,7 +173,8 @@ struct RbTile {
             const float* bs = Bs + cur * Cfg::B_ELEMS;
 #pragma unroll
             for (int k = 0; k < Cfg::BK; ++k) {
-                float a[Cfg::SR], b[Cfg::S];
+                float a[Cfg::SR];
+                uint64_t b2[Cfg::S / 2];
 #pragma unroll
                 for (int rr = 0; rr < Cfg::SR / 4; ++rr) {
                     const float4 v =
@@ -172,15 +188,15 @@ struct RbTile {
                 for (int ww = 0; ww < Cfg::S / 4; ++ww) {
                     const float4 v =
                         *reinterpret_cast<const float4*>(bs + k * Cfg::LDBS + ww * 4 * Cfg::B1 + 4 * t1);
-                    b[4 * ww + 0] = v.x;
-                    b[4 * ww + 1] = v.y;
-                    b[4 * ww + 2] = v.z;
-                    b[4 * ww + 3] = v.w;
+                    b2[2 * ww + 0] = pack2(v.x, v.y);
+                    b2[2 * ww + 1] = pack2(v.z, v.w);
                 }
 #pragma unroll
-                for (int i = 0; i < Cfg::SR; ++i)
+                for (int i = 0; i < Cfg::SR; ++i) {
+                    const uint64_t ai = pack2(a[i], a[i]);
 #pragma unroll
-                    for (int j = 0; j < Cfg::S; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                    for (int j = 0; j < Cfg::S / 2; ++j) fma2(acc2[i][j], ai, b2[j]);
+                }
             }
             if (t + 1 < nk) {
                 store_a(ra, As + (cur ^ 1) * Cfg::A_ELEMS, tid);
@@ -201,9 +217,10 @@ struct RbTile {
                     const int gn = col0 + ww * 4 * Cfg::B1 + 4 * t1;
                     float* cp = C + (size_t)gm * ldc + gn;
                     const int i = 4 * rr + v;
+                    const float o4[4] = {lo32(acc2[i][2 * ww]), hi32(acc2[i][2 * ww]),
+                                         lo32(acc2[i][2 * ww + 1]), hi32(acc2[i][2 * ww + 1])};
                     if (vecC && gn + 3 < N) {
-                        float4 o = make_float4(acc[i][4 * ww], acc[i][4 * ww + 1], acc[i][4 * ww + 2],
-                                               acc[i][4 * ww + 3]);
+                        float4 o = make_float4(o4[0], o4[1], o4[2], o4[3]);
                         if (beta) {
                             const float4 c = *reinterpret_cast<const float4*>(cp);
                             o.x += c.x;
@@ -215,7 +232,7 @@ struct RbTile {
                     } else {
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (gn + u < N) cp[u] = beta ? cp[u] + acc[i][4 * ww + u] : acc[i][4 * ww + u];
+                            if (gn + u < N) cp[u] = beta ? cp[u] + o4[u] : o4[u];
                     }
                 }
             }

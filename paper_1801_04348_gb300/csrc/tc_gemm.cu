@@ -55,14 +55,17 @@ struct TcCfg {
     // chunk carries its own scales.  Split: 512-deep chunks bound the growth
     // of the tensor-core accumulator, the dominant error at large K.
     static constexpr int CHUNK = MODE == MODE_FP8 ? 1 : (MODE == MODE_SPLIT ? 8 : 0);
-    static constexpr int EPI_WARPS = CHUNK == 0 ? 4 : (BN == 256 ? 16 : 8);
+    static constexpr int EPI_WARPS = CHUNK == 0 ? 4 : 8;
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
-    static constexpr int TMEM_COLS = 2 * BN;                // two FP32 accumulators
+    // tensor-memory accumulators in flight: FP8 with 128-wide tiles keeps four
+    // chunk accumulators so the MMA can run three chunks ahead of the epilogue
+    static constexpr int ACC_BUFS = (MODE == MODE_FP8 && BN == 128) ? 4 : 2;
+    static constexpr int TMEM_COLS = ACC_BUFS * BN;
     static constexpr int SMEM_RAW = STAGES * STAGE_BYTES + 1024;
     // at least 116 KB so that one CTA owns the SM (and its tensor memory)
     static constexpr int SMEM = SMEM_RAW > 118784 ? SMEM_RAW : 118784;
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation is a power of two");
-    static_assert(CHUNK == 0 || BN / (EPI_WARPS / 4) == 64, "64 promoted columns per warp");
+    static_assert(CHUNK == 0 || BN / (EPI_WARPS / 4) <= 128, "promoted columns per warp");
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -225,8 +228,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[Cfg::STAGES];
     __shared__ uint64_t empty_bar[Cfg::STAGES];
-    __shared__ uint64_t accf_bar[2];
-    __shared__ uint64_t acce_bar[2];
+    __shared__ uint64_t accf_bar[Cfg::ACC_BUFS];
+    __shared__ uint64_t acce_bar[Cfg::ACC_BUFS];
     __shared__ uint64_t drain_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < Cfg::ACC_BUFS; ++b) {
             mbar_init(&accf_bar[b], 1);
             mbar_init(&acce_bar[b], Cfg::EPI_WARPS * 32);
         }
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     }
                     if (Cfg::CHUNK > 0 && (kin == Cfg::CHUNK - 1 || kb == nkb - 1)) {
                         mma_commit(&accf_bar[acc]);
-                        if (++acc == 2) {
+                        if (++acc == Cfg::ACC_BUFS) {
                             acc = 0;
                             acc_phase ^= 1u;
                         }
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 if (!ok) break;
                 if (Cfg::CHUNK == 0) {
                     mma_commit(&accf_bar[acc]);
-                    if (++acc == 2) {
+                    if (++acc == Cfg::ACC_BUFS) {
                         acc = 0;
                         acc_phase ^= 1u;
                     }
@@ -465,28 +468,35 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     while (!mbar_try_wait(&accf_bar[acc], acc_phase)) {
                     }
                     tc_fence_after();
+                    // chunk sum times sA * sB (FP8: the tile scales of this 128-deep chunk)
+                    const float sc = Cfg::MODE == MODE_FP8
+                                         ? __ldg(p.sA + (size_t)tm * ksa + ch) *
+                                               __ldg(p.sB + (size_t)ch * nsb + n0 / 128)
+                                         : 1.f;
+                    // loads issued per wait: both of a 64-column slice, else 32 columns
+                    // at a time (128-column slices keep 128 accumulators in registers)
+                    constexpr int NB = Cfg::BN / (Cfg::EPI_WARPS / 4) == 64 ? 2 : 1;
 #pragma unroll
-                    for (int c = 0; c < ncol / 32; ++c) {
-                        uint32_t r[32];
-                        tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) +
-                                      (uint32_t)(acc * Cfg::BN + col0 + c * 32),
-                                  r);
+                    for (int c0 = 0; c0 < ncol / 32; c0 += NB) {
+                        uint32_t r[NB][32];
+#pragma unroll
+                        for (int c = 0; c < NB; ++c)
+                            tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) +
+                                          (uint32_t)(acc * Cfg::BN + col0 + (c0 + c) * 32),
+                                      r[c]);
                         tmem_ld_wait();
-                        if (Cfg::MODE == MODE_FP8) {
-                            // chunk sum times sA * sB (the tile scales of this 128-deep chunk)
-                            const float sc = __ldg(p.sA + (size_t)tm * ksa + ch) *
-                                             __ldg(p.sB + (size_t)ch * nsb + n0 / 128);
 #pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                accr[c * 32 + j] = fmaf(__uint_as_float(r[j]), sc, accr[c * 32 + j]);
-                        } else {
+                        for (int c = 0; c < NB; ++c)
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) accr[c * 32 + j] += __uint_as_float(r[j]);
-                        }
+                            for (int j = 0; j < 32; ++j) {
+                                float& a = accr[(c0 + c) * 32 + j];
+                                if (Cfg::MODE == MODE_FP8) a = fmaf(__uint_as_float(r[c][j]), sc, a);
+                                else a += __uint_as_float(r[c][j]);
+                            }
                     }
                     tc_fence_before();
                     mbar_arrive(&acce_bar[acc]);
-                    if (++acc == 2) {
+                    if (++acc == Cfg::ACC_BUFS) {
                         acc = 0;
                         acc_phase ^= 1u;
                     }
@@ -555,7 +565,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 }
                 tc_fence_before();
                 mbar_arrive(&acce_bar[acc]);
-                if (++acc == 2) {
+                if (++acc == Cfg::ACC_BUFS) {
                     acc = 0;
                     acc_phase ^= 1u;
                 }
