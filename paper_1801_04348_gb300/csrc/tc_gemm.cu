@@ -656,6 +656,7 @@ static TcVariant tcv(int family) {
 static const TcVariant* tc_table(int* n) {
     static const TcVariant t[] = {
         tcv<MODE_BF16, 256, 4>(PGK_FAM_TC_BF16),   tcv<MODE_BF16, 128, 6>(PGK_FAM_TC_BF16),
+        tcv<MODE_BF16, 256, 3>(PGK_FAM_TC_BF16),   tcv<MODE_BF16, 128, 4>(PGK_FAM_TC_BF16),
         tcv<MODE_SPLIT, 128, 3>(PGK_FAM_TC_SPLIT), tcv<MODE_SPLIT, 256, 2>(PGK_FAM_TC_SPLIT),
         tcv<MODE_FP8, 128, 6>(PGK_FAM_TC_FP8),     tcv<MODE_FP8, 256, 4>(PGK_FAM_TC_FP8),
     };
