@@ -60,8 +60,12 @@ typedef enum {
  *                  tile, tcgen05 tensor cores, FP32 accumulate per 128-deep chunk,
  *   PGK_SPLIT_BF16 x = hi + lo with hi = bf16(x), lo = bf16(x - hi); C is the sum
  *                  of the three products lo*hi + hi*lo + hi*hi in one FP32
- *                  accumulator (lo*lo dropped). */
-typedef enum { PGK_F32 = 0, PGK_BF16 = 1, PGK_FP8_E4M3 = 2, PGK_SPLIT_BF16 = 3 } pgk_dtype;
+ *                  accumulator (lo*lo dropped),
+ *   PGK_I32        int32 operands and result (the paper's data type, Fig.
+ *                  "cudamul"), SIMT multiply-add modulo 2^32 (two's complement);
+ *                  with pgk_gemm the A, B, C pointers then hold int32 words
+ *                  (pgk_gemm_i32 is the typed form). */
+typedef enum { PGK_F32 = 0, PGK_BF16 = 1, PGK_FP8_E4M3 = 2, PGK_SPLIT_BF16 = 3, PGK_I32 = 4 } pgk_dtype;
 
 /* Machine parameters R_1..R_s (Section 3.2), read with cudaGetDeviceProperties.
  * smem_* are in bytes (the paper counts words).  max_regs_per_thread is the
@@ -105,7 +109,10 @@ typedef enum {
     PGK_FAM_DIRECT = 2,   /* no shared memory, one output per thread              */
     PGK_FAM_TC_BF16 = 3,  /* tcgen05 kind::f16, BF16 operands                     */
     PGK_FAM_TC_SPLIT = 4, /* tcgen05 kind::f16, three BF16 products               */
-    PGK_FAM_TC_FP8 = 5    /* tcgen05 kind::f8f6f4, per-tile scaled E4M3           */
+    PGK_FAM_TC_FP8 = 5,   /* tcgen05 kind::f8f6f4, per-tile scaled E4M3           */
+    PGK_FAM_PAPER_I32 = 6,  /* the paper family on int32                          */
+    PGK_FAM_RB_I32 = 7,     /* the register-blocked family on int32               */
+    PGK_FAM_DIRECT_I32 = 8  /* the no-shared-memory leaf on int32                 */
 } pgk_family;
 
 /* A leaf chosen by the case discussion: the variant to launch and the values of
@@ -196,6 +203,13 @@ PGK_API pgk_status pgk_select_case_regs(const pgk_machine* machine, const int* r
 PGK_API pgk_status pgk_gemm(int M, int N, int K, pgk_dtype dtype, const float* A, int lda,
                     const float* B, int ldb, float* C, int ldc, int beta,
                     const pgk_params* prog, void* stream);
+
+/* C = A*B (beta = 0) or C += A*B (beta = 1) on int32 matrices, modulo 2^32:
+ * the paper's own data type (Fig. "cudamul").  Same case discussion, variants
+ * and errors as pgk_gemm with dtype PGK_I32 (SIMT only). */
+PGK_API pgk_status pgk_gemm_i32(int M, int N, int K, const int32_t* A, int lda, const int32_t* B,
+                                int ldb, int32_t* C, int ldc, int beta, const pgk_params* prog,
+                                void* stream);
 
 /* Launch the SIMT variant of a case returned by pgk_select_case(_regs) on FP32
  * operands (lets a caller run any leaf, e.g. one chosen for a mock machine).

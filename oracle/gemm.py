@@ -48,6 +48,9 @@ def _load():
                            dp, i64, dp, i64, ctypes.c_int]
         lib.oracle_gemm_longdouble.restype = ctypes.c_int
         lib.oracle_gemm_longdouble.argtypes = [i64, i64, i64, dp, dp, dp]
+        lib.oracle_gemm_i32_wrap.restype = ctypes.c_int
+        lib.oracle_gemm_i32_wrap.argtypes = [i64, i64, i64, fp, i64, fp, i64, ctypes.c_int, dp, i64,
+                                             dp, i64]
         lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_max_threads.argtypes = []
         _lib = lib
@@ -112,6 +115,26 @@ def gemm_longdouble(A: np.ndarray, B: np.ndarray) -> np.ndarray:
     N = B.shape[1]
     C = np.empty((M, N), dtype=np.float64)
     _load().oracle_gemm_longdouble(M, N, K, _ptr(A), _ptr(B), _ptr(C))
+    return C
+
+
+def gemm_i32(A: np.ndarray, B: np.ndarray, C0: np.ndarray | None = None,
+             beta: int = 0) -> np.ndarray:
+    """int32 C = beta*C0 + A@B modulo 2^32 (two's complement), the paper's data
+    type; A (M x K), B (K x N) int32 row-major."""
+    A = np.ascontiguousarray(A, dtype=np.int32)
+    B = np.ascontiguousarray(B, dtype=np.int32)
+    if A.shape[1] != B.shape[0]:
+        raise ValueError("shape mismatch")
+    M, K = A.shape
+    N = B.shape[1]
+    if beta:
+        C0 = np.ascontiguousarray(C0, dtype=np.int32)
+    C = np.empty((M, N), dtype=np.int32)
+    rc = _load().oracle_gemm_i32_wrap(M, N, K, _ptr(A), K, _ptr(B), N, int(bool(beta)),
+                                      _ptr(C0) if beta else None, N, _ptr(C), N)
+    if rc != 0:
+        raise RuntimeError("oracle_gemm_i32_wrap failed")
     return C
 
 

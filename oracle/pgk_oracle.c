@@ -100,3 +100,25 @@ int oracle_max_threads(void) {
     return 1;
 #endif
 }
+
+/* int32 form of the same definition, the paper's own data type (Fig.
+ * "cudamul" declares int *a, *b, *c): C = beta*C0 + A*B evaluated modulo 2^32
+ * and read back as two's complement.  Unsigned 32-bit arithmetic in C wraps
+ * modulo 2^32 by definition, so every product and sum is taken there. */
+int oracle_gemm_i32_wrap(int64_t M, int64_t N, int64_t K, const int32_t* A, int64_t lda,
+                         const int32_t* B, int64_t ldb, int beta, const int32_t* C0,
+                         int64_t ldc0, int32_t* C, int64_t ldc) {
+    if (M < 0 || N < 0 || K < 0) return -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < M; ++i) {
+        for (int64_t j = 0; j < N; ++j) {
+            uint32_t acc = beta ? (uint32_t)C0[i * ldc0 + j] : 0u;
+            for (int64_t k = 0; k < K; ++k)
+                acc += (uint32_t)A[i * lda + k] * (uint32_t)B[k * ldb + j];
+            C[i * ldc + j] = (int32_t)acc;
+        }
+    }
+    return 0;
+}

@@ -94,26 +94,26 @@ std::vector<Variant>& registry() {
     return g_registry;
 }
 
-int find_paper_variant(int s, int regopt) {
+int find_paper_variant(int family, int s, int regopt) {
     std::vector<Variant>& r = registry();
     for (size_t i = 0; i < r.size(); ++i)
-        if (r[i].info.family == PGK_FAM_PAPER && r[i].info.s == s && r[i].info.regopt == regopt)
+        if (r[i].info.family == family && r[i].info.s == s && r[i].info.regopt == regopt)
             return (int)i;
     return -1;
 }
 
-int find_direct_variant(int regopt) {
+int find_direct_variant(int family, int regopt) {
     std::vector<Variant>& r = registry();
     for (size_t i = 0; i < r.size(); ++i)
-        if (r[i].info.family == PGK_FAM_DIRECT && r[i].info.regopt == regopt) return (int)i;
+        if (r[i].info.family == family && r[i].info.regopt == regopt) return (int)i;
     return -1;
 }
 
-int find_rb_variant(int B0, int B1, int sr, int s, int tile) {
+int find_rb_variant(int family, int B0, int B1, int sr, int s, int tile) {
     std::vector<Variant>& r = registry();
     for (size_t i = 0; i < r.size(); ++i) {
         const pgk_variant_info& v = r[i].info;
-        if (v.family == PGK_FAM_RB && v.B0 == B0 && v.B1 == B1 && v.sr == sr && v.s == s &&
+        if (v.family == family && v.B0 == B0 && v.B1 == B1 && v.sr == sr && v.s == s &&
             v.tile == tile)
             return (int)i;
     }
@@ -162,7 +162,8 @@ long long smem_rb(int B0, int B1, int sr, int s, int BK) {
 // -------------------------------------------------------- case discussion
 // Program state of Algorithm 2 for the GEMM family.
 struct Prog {
-    int family;  // PGK_FAM_PAPER / RB / DIRECT
+    int family;  // PGK_FAM_PAPER / RB / DIRECT (logical family; int32 mapped by is_int)
+    int is_int;  // int32 variants (PGK_I32)
     int cache;   // (4a) / (4b)
     int s, sr;   // effective granularity
     int regopt;  // strategy "1" applied
@@ -201,9 +202,11 @@ struct RegSource {
 };
 
 static int variant_of(const Prog& p, int B0, int B1, int BK) {
-    if (p.family == PGK_FAM_DIRECT) return find_direct_variant(p.regopt);
-    if (p.family == PGK_FAM_PAPER) return find_paper_variant(p.s, p.regopt);
-    return find_rb_variant(B0, B1, p.sr, p.s, BK);
+    if (p.family == PGK_FAM_DIRECT)
+        return find_direct_variant(p.is_int ? PGK_FAM_DIRECT_I32 : PGK_FAM_DIRECT, p.regopt);
+    if (p.family == PGK_FAM_PAPER)
+        return find_paper_variant(p.is_int ? PGK_FAM_PAPER_I32 : PGK_FAM_PAPER, p.s, p.regopt);
+    return find_rb_variant(p.is_int ? PGK_FAM_RB_I32 : PGK_FAM_RB, B0, B1, p.sr, p.s, BK);
 }
 
 static pgk_status regs_of(const Prog& p, int B0, int B1, int BK, const RegSource& src, long long* out) {
@@ -269,7 +272,7 @@ static long long limit_of(int c, const pgk_machine& m) {
 // r_1..r_i back on the counter stack (top = r_i, Remark "stacks"); with no such
 // strategy the branch is dropped and the point has no case (INFEASIBLE).
 static pgk_status simt_case(const pgk_machine* m, const RegSource& src, const pgk_params* prog,
-                            pgk_case* out) {
+                            int is_int, pgk_case* out) {
     const int B0 = prog->B0, B1 = prog->B1, s = prog->s;
     const int sr = prog->sr <= 0 ? 1 : prog->sr;
     const int BK = prog->tile == 0 ? B0 : prog->tile;
@@ -284,6 +287,7 @@ static pgk_status simt_case(const pgk_machine* m, const RegSource& src, const pg
     }
     Prog p;
     p.family = sr == 1 ? PGK_FAM_PAPER : PGK_FAM_RB;
+    p.is_int = is_int;
     p.cache = 1;
     p.s = s;
     p.sr = sr;
@@ -293,7 +297,8 @@ static pgk_status simt_case(const pgk_machine* m, const RegSource& src, const pg
         set_error("paper-form variants exist for s in {1,2,4,8}, got %d", s);
         return PGK_ERR_UNSUPPORTED;
     }
-    if (p.family == PGK_FAM_RB && find_rb_variant(B0, B1, sr, s, BK) < 0) {
+    if (p.family == PGK_FAM_RB &&
+        find_rb_variant(is_int ? PGK_FAM_RB_I32 : PGK_FAM_RB, B0, B1, sr, s, BK) < 0) {
         set_error("register-blocked variant (B0=%d,B1=%d,sr=%d,s=%d,tile=%d) is not compiled", B0,
                   B1, sr, s, BK);
         return PGK_ERR_UNSUPPORTED;
@@ -333,7 +338,10 @@ static pgk_status simt_case(const pgk_machine* m, const RegSource& src, const pg
     pgk_case cs;
     memset(&cs, 0, sizeof(cs));
     cs.leaf = !p.cache ? PGK_LEAF_3B4B : (p.gran ? PGK_LEAF_3B4A : PGK_LEAF_4A3A);
-    cs.family = p.family;
+    cs.family = !is_int ? p.family
+                        : (p.family == PGK_FAM_PAPER ? PGK_FAM_PAPER_I32
+                                                     : p.family == PGK_FAM_RB ? PGK_FAM_RB_I32
+                                                                              : PGK_FAM_DIRECT_I32);
     cs.regopt = p.regopt;
     cs.variant_id = variant_of(p, B0, B1, BK);
     long long sm = 0, rg = 0;
@@ -367,10 +375,10 @@ static pgk_status select_any(const pgk_machine* m, const int* regs_table, int M,
     }
     pgk_status st = check_dims(M, N, K);
     if (st != PGK_OK) return st;
-    if (dtype == PGK_F32) {
+    if (dtype == PGK_F32 || dtype == PGK_I32) {
         RegSource src;
         src.table = regs_table;
-        return simt_case(m, src, prog, out);
+        return simt_case(m, src, prog, dtype == PGK_I32, out);
     }
     if (dtype == PGK_BF16 || dtype == PGK_FP8_E4M3 || dtype == PGK_SPLIT_BF16)
         return tc_select(m, M, N, K, dtype, prog, out);
@@ -428,7 +436,7 @@ static pgk_status check_gemm_args(int M, int N, int K, const void* A, int lda, c
 
 pgk_params default_params(int M, int N, int K, pgk_dtype dtype) {
     pgk_params p;
-    if (dtype == PGK_F32) {
+    if (dtype == PGK_F32 || dtype == PGK_I32) {
         if ((long long)M * N >= 2048LL * 2048) {
             p.B0 = 16; p.B1 = 16; p.s = 8; p.sr = 8; p.tile = 8;
         } else if ((long long)M * N >= 256LL * 256) {
@@ -531,7 +539,9 @@ pgk_status pgk_gemm_case(const pgk_case* c, int M, int N, int K, const float* A,
     }
     pgk_status st = check_gemm_args(M, N, K, A, lda, B, ldb, C, ldc);
     if (st != PGK_OK) return st;
-    if (c->family != PGK_FAM_PAPER && c->family != PGK_FAM_RB && c->family != PGK_FAM_DIRECT) {
+    if (c->family != PGK_FAM_PAPER && c->family != PGK_FAM_RB && c->family != PGK_FAM_DIRECT &&
+        c->family != PGK_FAM_PAPER_I32 && c->family != PGK_FAM_RB_I32 &&
+        c->family != PGK_FAM_DIRECT_I32) {
         set_error("pgk_gemm_case runs SIMT cases only");
         return PGK_ERR_INVALID_ARG;
     }
@@ -554,10 +564,18 @@ pgk_status pgk_gemm(int M, int N, int K, pgk_dtype dtype, const float* A, int ld
     pgk_case c;
     st = select_any(&m, NULL, M, N, K, dtype, &p, &c);
     if (st != PGK_OK) return st;
-    if (dtype == PGK_F32)
+    if (dtype == PGK_F32 || dtype == PGK_I32)
         return run_simt_case(c, M, N, K, A, lda, B, ldb, C, ldc, beta, (cudaStream_t)stream);
     return tc_gemm_fp32_inputs(c, M, N, K, dtype, A, lda, B, ldb, C, ldc, beta,
                                (cudaStream_t)stream);
+}
+
+pgk_status pgk_gemm_i32(int M, int N, int K, const int32_t* A, int lda, const int32_t* B, int ldb,
+                        int32_t* C, int ldc, int beta, const pgk_params* prog, void* stream) {
+    // int32 words travel through the same 32-bit data paths as FP32
+    return pgk_gemm(M, N, K, PGK_I32, reinterpret_cast<const float*>(A), lda,
+                    reinterpret_cast<const float*>(B), ldb, reinterpret_cast<float*>(C), ldc, beta,
+                    prog, stream);
 }
 
 pgk_status pgk_shutdown(void) {

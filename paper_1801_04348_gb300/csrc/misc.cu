@@ -109,14 +109,14 @@ void tune_cache_release() {
 }
 
 // -------------------------------------------------------- default candidates
-static int simt_candidates(pgk_params* out, int cap) {
+static int simt_candidates(int rb_family, pgk_params* out, int cap) {
     // every compiled register-blocked variant plus the paper-form grid of the
     // paper's experiment shapes (B0, B1 in {8,16,32}, s in {1,2,4}, BK = B0)
     std::vector<pgk_params> c;
     std::vector<Variant>& r = registry();
     for (size_t i = 0; i < r.size(); ++i) {
         const pgk_variant_info& v = r[i].info;
-        if (v.family != PGK_FAM_RB) continue;
+        if (v.family != rb_family) continue;
         pgk_params p = {v.B0, v.B1, v.s, v.sr, v.tile};
         c.push_back(p);
     }
@@ -234,7 +234,8 @@ pgk_status pgk_tune_cache_load(const char* path) {
 }
 
 int pgk_default_candidates(pgk_dtype dtype, pgk_params* out, int cap) {
-    if (dtype == PGK_F32) return simt_candidates(out, cap);
+    if (dtype == PGK_F32) return simt_candidates(PGK_FAM_RB, out, cap);
+    if (dtype == PGK_I32) return simt_candidates(PGK_FAM_RB_I32, out, cap);
     if (dtype == PGK_BF16 || dtype == PGK_SPLIT_BF16 || dtype == PGK_FP8_E4M3)
         return tc_candidates(dtype, out, cap);
     return 0;

@@ -53,9 +53,9 @@ void register_tc_variants(std::vector<Variant>& v);
 
 // Registry access (host.cu).
 std::vector<Variant>& registry();
-int find_paper_variant(int s, int regopt);
-int find_direct_variant(int regopt);
-int find_rb_variant(int B0, int B1, int sr, int s, int tile);
+int find_paper_variant(int family, int s, int regopt);
+int find_direct_variant(int family, int regopt);
+int find_rb_variant(int family, int B0, int B1, int sr, int s, int tile);
 // Register count of a variant on the current device (-1 if unavailable).
 int variant_regs(int id);
 

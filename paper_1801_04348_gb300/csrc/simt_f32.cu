@@ -16,7 +16,7 @@
 namespace pgk {
 
 // ----------------------------------------------------------- paper family
-template <int S>
+template <int S, bool INT>
 __device__ __forceinline__ void paper_body(const SimtArgs& p) {
     extern __shared__ float smem_paper[];
     const int B0 = p.B0, B1 = p.B1, BK = p.BK;
@@ -29,7 +29,7 @@ __device__ __forceinline__ void paper_body(const SimtArgs& p) {
     float* Bs = smem_paper + B0 * BK;  // BK x BN
     const int row = bm * B0 + t0;
     const int col0 = bn * BN + t1;
-    float acc[S];
+    float acc[S];   // FP32 values, or int32 words for INT
 #pragma unroll
     for (int w = 0; w < S; ++w) acc[w] = 0.f;
 
@@ -49,7 +49,12 @@ __device__ __forceinline__ void paper_body(const SimtArgs& p) {
         for (int k = 0; k < kmax; ++k) {
             const float a = As[t0 * BK + k];
 #pragma unroll
-            for (int w = 0; w < S; ++w) acc[w] = fmaf(a, Bs[k * BN + t1 + w * B1], acc[w]);
+            for (int w = 0; w < S; ++w) {
+                const float b = Bs[k * BN + t1 + w * B1];
+                acc[w] = INT ? __uint_as_float(__float_as_uint(acc[w]) +
+                                               __float_as_uint(a) * __float_as_uint(b))
+                             : fmaf(a, b, acc[w]);
+            }
         }
         __syncthreads();
     }
@@ -59,39 +64,40 @@ __device__ __forceinline__ void paper_body(const SimtArgs& p) {
             const int col = col0 + w * B1;
             if (col < p.N) {
                 float* cp = p.C + (size_t)row * p.ldc + col;
-                *cp = p.beta ? *cp + acc[w] : acc[w];
+                *cp = p.beta ? add32<INT>(*cp, acc[w]) : acc[w];
             }
         }
     }
 }
 
-template <int S>
-__global__ void k_paper(SimtArgs p) { paper_body<S>(p); }
+template <int S, bool INT>
+__global__ void k_paper(SimtArgs p) { paper_body<S, INT>(p); }
 
 // Register-pressure strategy "1": the same source compiled so that a block of
 // 1024 threads fits the 64K register file (at most 64 registers per thread).
-template <int S>
-__global__ void __launch_bounds__(1024, 1) k_paper_cap(SimtArgs p) { paper_body<S>(p); }
+template <int S, bool INT>
+__global__ void __launch_bounds__(1024, 1) k_paper_cap(SimtArgs p) { paper_body<S, INT>(p); }
 
-template <int S, bool CAP>
+template <int S, bool CAP, bool INT>
 static cudaError_t launch_paper(const SimtArgs& p, int smem, cudaStream_t st) {
     const int BN = p.B1 * S;
     const long long tiles = (long long)((p.M + p.B0 - 1) / p.B0) * ((p.N + BN - 1) / BN);
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const void* f = CAP ? (const void*)k_paper_cap<S> : (const void*)k_paper<S>;
+    const void* f = CAP ? (const void*)k_paper_cap<S, INT> : (const void*)k_paper<S, INT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
     dim3 block(p.B1, p.B0);
     if (CAP)
-        k_paper_cap<S><<<(unsigned)tiles, block, smem, st>>>(p);
+        k_paper_cap<S, INT><<<(unsigned)tiles, block, smem, st>>>(p);
     else
-        k_paper<S><<<(unsigned)tiles, block, smem, st>>>(p);
+        k_paper<S, INT><<<(unsigned)tiles, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------- direct family
+template <bool INT>
 __device__ __forceinline__ void direct_body(const SimtArgs& p) {
     const int B0 = p.B0, B1 = p.B1;
     const int tiles_n = (p.N + B1 - 1) / B1;
@@ -101,49 +107,56 @@ __device__ __forceinline__ void direct_body(const SimtArgs& p) {
     const float* a = p.A + (size_t)row * p.lda;
     const float* b = p.B + col;
     float acc = 0.f;
-    for (int k = 0; k < p.K; ++k) acc = fmaf(__ldg(a + k), __ldg(b + (size_t)k * p.ldb), acc);
+    for (int k = 0; k < p.K; ++k) {
+        const float x = __ldg(a + k), y = __ldg(b + (size_t)k * p.ldb);
+        acc = INT ? __uint_as_float(__float_as_uint(acc) + __float_as_uint(x) * __float_as_uint(y))
+                  : fmaf(x, y, acc);
+    }
     float* cp = p.C + (size_t)row * p.ldc + col;
-    *cp = p.beta ? *cp + acc : acc;
+    *cp = p.beta ? add32<INT>(*cp, acc) : acc;
 }
 
-__global__ void k_direct(SimtArgs p) { direct_body(p); }
-__global__ void __launch_bounds__(1024, 1) k_direct_cap(SimtArgs p) { direct_body(p); }
+template <bool INT>
+__global__ void k_direct(SimtArgs p) { direct_body<INT>(p); }
+template <bool INT>
+__global__ void __launch_bounds__(1024, 1) k_direct_cap(SimtArgs p) { direct_body<INT>(p); }
 
-template <bool CAP>
+template <bool CAP, bool INT>
 static cudaError_t launch_direct(const SimtArgs& p, int, cudaStream_t st) {
     const long long tiles = (long long)((p.M + p.B0 - 1) / p.B0) * ((p.N + p.B1 - 1) / p.B1);
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     dim3 block(p.B1, p.B0);
     if (CAP)
-        k_direct_cap<<<(unsigned)tiles, block, 0, st>>>(p);
+        k_direct_cap<INT><<<(unsigned)tiles, block, 0, st>>>(p);
     else
-        k_direct<<<(unsigned)tiles, block, 0, st>>>(p);
+        k_direct<INT><<<(unsigned)tiles, block, 0, st>>>(p);
     return cudaGetLastError();
 }
 
 // -------------------------------------------------------------- rb family
-template <class Cfg>
+template <class Cfg, bool INT>
 __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) k_rb(SimtArgs p) {
     extern __shared__ float4 smem_rb4[];
     const int tiles_m = (p.M + Cfg::BM - 1) / Cfg::BM;
     const int tiles_n = (p.N + Cfg::BN - 1) / Cfg::BN;
     int bm, bn;
     grouped_tile_coords(blockIdx.x, tiles_m, tiles_n, bm, bn);
-    RbTile<Cfg>::run(p.A, p.lda, p.B, p.ldb, p.C, p.ldc, p.M, p.N, p.K, bm * Cfg::BM, bn * Cfg::BN,
-                     p.beta, p.vecA, p.vecB, p.vecC, reinterpret_cast<float*>(smem_rb4));
+    RbTile<Cfg, INT>::run(p.A, p.lda, p.B, p.ldb, p.C, p.ldc, p.M, p.N, p.K, bm * Cfg::BM,
+                          bn * Cfg::BN, p.beta, p.vecA, p.vecB, p.vecC,
+                          reinterpret_cast<float*>(smem_rb4));
 }
 
-template <class Cfg>
+template <class Cfg, bool INT>
 static cudaError_t launch_rb(const SimtArgs& p, int, cudaStream_t st) {
     const long long tiles =
         (long long)((p.M + Cfg::BM - 1) / Cfg::BM) * ((p.N + Cfg::BN - 1) / Cfg::BN);
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if (Cfg::SMEM > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_rb<Cfg>,
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_rb<Cfg, INT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e != cudaSuccess) return e;
     }
-    k_rb<Cfg><<<(unsigned)tiles, Cfg::NT, Cfg::SMEM, st>>>(p);
+    k_rb<Cfg, INT><<<(unsigned)tiles, Cfg::NT, Cfg::SMEM, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -166,24 +179,37 @@ static Variant make_variant(int family, int s, int sr, int B0, int B1, int tile,
     return v;
 }
 
-template <int B0, int B1, int SR, int S, int BK>
+template <int B0, int B1, int SR, int S, int BK, bool INT = false>
 static void add_rb(std::vector<Variant>& v) {
     typedef RbCfg<B0, B1, SR, S, BK> Cfg;
-    v.push_back(make_variant(PGK_FAM_RB, S, SR, B0, B1, BK, 0, (const void*)k_rb<Cfg>,
-                             launch_rb<Cfg>, Cfg::SMEM));
+    v.push_back(make_variant(INT ? PGK_FAM_RB_I32 : PGK_FAM_RB, S, SR, B0, B1, BK, 0,
+                             (const void*)k_rb<Cfg, INT>, launch_rb<Cfg, INT>, Cfg::SMEM));
+}
+
+template <bool INT>
+static void add_paper_and_direct(std::vector<Variant>& v) {
+    const int fp = INT ? PGK_FAM_PAPER_I32 : PGK_FAM_PAPER;
+    const int fd = INT ? PGK_FAM_DIRECT_I32 : PGK_FAM_DIRECT;
+    v.push_back(make_variant(fp, 1, 1, 0, 0, 0, 0, (const void*)k_paper<1, INT>, launch_paper<1, false, INT>, 0));
+    v.push_back(make_variant(fp, 2, 1, 0, 0, 0, 0, (const void*)k_paper<2, INT>, launch_paper<2, false, INT>, 0));
+    v.push_back(make_variant(fp, 4, 1, 0, 0, 0, 0, (const void*)k_paper<4, INT>, launch_paper<4, false, INT>, 0));
+    v.push_back(make_variant(fp, 8, 1, 0, 0, 0, 0, (const void*)k_paper<8, INT>, launch_paper<8, false, INT>, 0));
+    v.push_back(make_variant(fp, 1, 1, 0, 0, 0, 1, (const void*)k_paper_cap<1, INT>, launch_paper<1, true, INT>, 0));
+    v.push_back(make_variant(fp, 2, 1, 0, 0, 0, 1, (const void*)k_paper_cap<2, INT>, launch_paper<2, true, INT>, 0));
+    v.push_back(make_variant(fp, 4, 1, 0, 0, 0, 1, (const void*)k_paper_cap<4, INT>, launch_paper<4, true, INT>, 0));
+    v.push_back(make_variant(fp, 8, 1, 0, 0, 0, 1, (const void*)k_paper_cap<8, INT>, launch_paper<8, true, INT>, 0));
+    v.push_back(make_variant(fd, 1, 1, 0, 0, 0, 0, (const void*)k_direct<INT>, launch_direct<false, INT>, 0));
+    v.push_back(make_variant(fd, 1, 1, 0, 0, 0, 1, (const void*)k_direct_cap<INT>, launch_direct<true, INT>, 0));
 }
 
 void register_simt_variants(std::vector<Variant>& v) {
-    v.push_back(make_variant(PGK_FAM_PAPER, 1, 1, 0, 0, 0, 0, (const void*)k_paper<1>, launch_paper<1, false>, 0));
-    v.push_back(make_variant(PGK_FAM_PAPER, 2, 1, 0, 0, 0, 0, (const void*)k_paper<2>, launch_paper<2, false>, 0));
-    v.push_back(make_variant(PGK_FAM_PAPER, 4, 1, 0, 0, 0, 0, (const void*)k_paper<4>, launch_paper<4, false>, 0));
-    v.push_back(make_variant(PGK_FAM_PAPER, 8, 1, 0, 0, 0, 0, (const void*)k_paper<8>, launch_paper<8, false>, 0));
-    v.push_back(make_variant(PGK_FAM_PAPER, 1, 1, 0, 0, 0, 1, (const void*)k_paper_cap<1>, launch_paper<1, true>, 0));
-    v.push_back(make_variant(PGK_FAM_PAPER, 2, 1, 0, 0, 0, 1, (const void*)k_paper_cap<2>, launch_paper<2, true>, 0));
-    v.push_back(make_variant(PGK_FAM_PAPER, 4, 1, 0, 0, 0, 1, (const void*)k_paper_cap<4>, launch_paper<4, true>, 0));
-    v.push_back(make_variant(PGK_FAM_PAPER, 8, 1, 0, 0, 0, 1, (const void*)k_paper_cap<8>, launch_paper<8, true>, 0));
-    v.push_back(make_variant(PGK_FAM_DIRECT, 1, 1, 0, 0, 0, 0, (const void*)k_direct, launch_direct<false>, 0));
-    v.push_back(make_variant(PGK_FAM_DIRECT, 1, 1, 0, 0, 0, 1, (const void*)k_direct_cap, launch_direct<true>, 0));
+    add_paper_and_direct<false>(v);
+    add_paper_and_direct<true>(v);
+    // int32 register-blocked variants
+    add_rb<16, 16, 8, 8, 8, true>(v);
+    add_rb<16, 16, 8, 8, 16, true>(v);
+    add_rb<16, 16, 4, 4, 8, true>(v);
+    add_rb<8, 8, 8, 8, 8, true>(v);
     // register-blocked variants: (B0, B1, sr, s, BK)
     add_rb<16, 16, 8, 8, 8>(v);
     add_rb<16, 16, 8, 8, 16>(v);

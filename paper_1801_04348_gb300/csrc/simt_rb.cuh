@@ -43,6 +43,13 @@ __device__ __forceinline__ void fma2(uint64_t& c, uint64_t a, uint64_t b) {
 __device__ __forceinline__ float lo32(uint64_t v) { return __uint_as_float((uint32_t)v); }
 __device__ __forceinline__ float hi32(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 
+// c + x on 32-bit words: FP32 addition, or int32 addition modulo 2^32.
+template <bool INT>
+__device__ __forceinline__ float add32(float c, float x) {
+    if (INT) return __uint_as_float(__float_as_uint(c) + __float_as_uint(x));
+    return c + x;
+}
+
 // Blocks visit tiles in groups of 8 tile-rows so that concurrently resident
 // blocks share panels of A and B in L2.
 __device__ __forceinline__ void grouped_tile_coords(int pid, int tiles_m, int tiles_n, int& bm,
@@ -57,7 +64,10 @@ __device__ __forceinline__ void grouped_tile_coords(int pid, int tiles_m, int ti
     bn = r / gm;
 }
 
-template <class Cfg>
+// INT = true: the same tile on int32 words (the paper's data type, Fig. "cudamul"):
+// the loaders move 32-bit words unchanged and the contraction is an unsigned
+// multiply-add, i.e. two's-complement arithmetic modulo 2^32.
+template <class Cfg, bool INT = false>
 struct RbTile {
     // Global -> registers: A tile rows [row0, row0+BM), cols [k0, k0+BK) as float4 along K.
     static __device__ __forceinline__ void load_a(float4 (&ra)[Cfg::LA], const float* __restrict__ A,
@@ -150,6 +160,7 @@ struct RbTile {
         float* As = smem;
         float* Bs = smem + 2 * Cfg::A_ELEMS;
         // acc2[i][2 ww + h] holds the outputs of row i, columns 4 ww + 2 h and 4 ww + 2 h + 1
+        // (FP32 pairs, or two int32 words for INT)
         uint64_t acc2[Cfg::SR][Cfg::S / 2];
 #pragma unroll
         for (int i = 0; i < Cfg::SR; ++i)
@@ -193,9 +204,20 @@ struct RbTile {
                 }
 #pragma unroll
                 for (int i = 0; i < Cfg::SR; ++i) {
-                    const uint64_t ai = pack2(a[i], a[i]);
+                    if (INT) {
+                        const uint32_t ai = __float_as_uint(a[i]);
 #pragma unroll
-                    for (int j = 0; j < Cfg::S / 2; ++j) fma2(acc2[i][j], ai, b2[j]);
+                        for (int j = 0; j < Cfg::S / 2; ++j) {
+                            const uint32_t lo = (uint32_t)acc2[i][j] + ai * (uint32_t)b2[j];
+                            const uint32_t hi = (uint32_t)(acc2[i][j] >> 32) +
+                                                ai * (uint32_t)(b2[j] >> 32);
+                            acc2[i][j] = ((uint64_t)hi << 32) | lo;
+                        }
+                    } else {
+                        const uint64_t ai = pack2(a[i], a[i]);
+#pragma unroll
+                        for (int j = 0; j < Cfg::S / 2; ++j) fma2(acc2[i][j], ai, b2[j]);
+                    }
                 }
             }
             if (t + 1 < nk) {
@@ -223,16 +245,16 @@ struct RbTile {
                         float4 o = make_float4(o4[0], o4[1], o4[2], o4[3]);
                         if (beta) {
                             const float4 c = *reinterpret_cast<const float4*>(cp);
-                            o.x += c.x;
-                            o.y += c.y;
-                            o.z += c.z;
-                            o.w += c.w;
+                            o.x = add32<INT>(o.x, c.x);
+                            o.y = add32<INT>(o.y, c.y);
+                            o.z = add32<INT>(o.z, c.z);
+                            o.w = add32<INT>(o.w, c.w);
                         }
                         *reinterpret_cast<float4*>(cp) = o;
                     } else {
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (gn + u < N) cp[u] = beta ? cp[u] + o4[u] : o4[u];
+                            if (gn + u < N) cp[u] = beta ? add32<INT>(cp[u], o4[u]) : o4[u];
                     }
                 }
             }

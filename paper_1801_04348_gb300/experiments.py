@@ -11,6 +11,7 @@ grouped    512 FP32 GEMMs, M, N, K log-uniform in [32, 2048] (multiples of 16, s
            normal(0,1) operands: one grouped persistent launch (eager and CUDA-graph
            replay, tile variant from pgk_autotune_grouped) against 512 separate pgk_gemm
            launches (eager and captured in one CUDA graph).
+mm         the paper's Table "mm" grid on GB300: int32, n = 2^10 and 2^11, (ub1, B0) x s.
 precision  8192^3, normal(0,1) and row-scaled by 10^uniform(-3,3): every form's step
            time (FP32 in/out, preparation included), kernel time on prepared operands,
            and relative Frobenius error on 64 sampled rows against the FP64 oracle.
@@ -215,6 +216,40 @@ def precision(dev, stream):
     return {"config": "precision 8192^3", "results": out}
 
 
+def mm_table(dev, stream):
+    """GB300 counterpart of the paper's Table "mm": the int32 paper-form kernel at
+    n = 2^10 and 2^11 for the paper's (ub1, B0) x s grid (tile = B0), plus the
+    tuned int32 register-blocked kernel; time and int32 Gop/s (2 n^3 / t)."""
+    import torch
+    grid = [(16, 4), (32, 4), (64, 4), (8, 8), (16, 8), (32, 8), (64, 8)]
+    rng = np.random.default_rng(0)
+    out = []
+    sh = stream.cuda_stream
+    for n in (1024, 2048):
+        A = torch.from_numpy(rng.integers(-100, 100, size=(n, n)).astype(np.int32)).to(dev)
+        B = torch.from_numpy(rng.integers(-100, 100, size=(n, n)).astype(np.int32)).to(dev)
+        C = torch.empty(n, n, dtype=torch.int32, device=dev)
+        rows = []
+        for ub1, b0 in grid:
+            for s in (2, 4):
+                p = pgk.params(b0, ub1, s)
+                run = lambda: pgk.gemm_i32(A, B, C, p, stream=sh)
+                run()
+                ms = _events_ms(run, 10, stream)
+                rows.append({"ub1": ub1, "B0": b0, "s": s, "ms": ms, "gops": 2.0 * n ** 3 / ms / 1e6})
+        best = min(rows, key=lambda r: r["ms"])
+        cands = pgk.default_candidates(pgk.I32)
+        tuned, _ = pgk.autotune(A, B, C, pgk.I32, candidates=[c for c in cands if c.sr > 1], reps=3,
+                                stream=stream)
+        run = lambda: pgk.gemm_i32(A, B, C, tuned, stream=sh)
+        run()
+        tms = _events_ms(run, 10, stream)
+        out.append({"n": n, "paper_grid": rows, "best_paper_form": best,
+                    "tuned_register_blocked": {"params": list(tuned.as_tuple()), "ms": tms,
+                                               "gops": 2.0 * n ** 3 / tms / 1e6}})
+    return {"config": "Table mm counterpart, int32", "sizes": out}
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
@@ -225,7 +260,8 @@ def main():
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
-    fns = {"config1": config1, "scale": scale, "grouped": grouped, "precision": precision}
+    fns = {"config1": config1, "scale": scale, "grouped": grouped, "precision": precision,
+           "mm": mm_table}
     for w in args.which:
         t0 = time.time()
         with torch.cuda.stream(stream):

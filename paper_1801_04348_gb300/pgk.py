@@ -17,10 +17,11 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpgk.so")
 PGK_OK = 0
 STATUS = {0: "PGK_OK", 1: "PGK_ERR_INVALID_ARG", 2: "PGK_ERR_INFEASIBLE", 3: "PGK_ERR_UNSUPPORTED",
           4: "PGK_ERR_ALIGNMENT", 5: "PGK_ERR_CUDA", 6: "PGK_ERR_TIMEOUT", 7: "PGK_ERR_NO_MEMORY"}
-F32, BF16, FP8_E4M3, SPLIT_BF16 = 0, 1, 2, 3
-DTYPES = {"f32": F32, "bf16": BF16, "fp8": FP8_E4M3, "split": SPLIT_BF16}
+F32, BF16, FP8_E4M3, SPLIT_BF16, I32 = 0, 1, 2, 3, 4
+DTYPES = {"f32": F32, "bf16": BF16, "fp8": FP8_E4M3, "split": SPLIT_BF16, "i32": I32}
 LEAF_4A3A, LEAF_3B4A, LEAF_3B4B = 0, 1, 2
-FAM_PAPER, FAM_RB, FAM_DIRECT, FAM_TC_BF16, FAM_TC_SPLIT, FAM_TC_FP8 = range(6)
+(FAM_PAPER, FAM_RB, FAM_DIRECT, FAM_TC_BF16, FAM_TC_SPLIT, FAM_TC_FP8, FAM_PAPER_I32, FAM_RB_I32,
+ FAM_DIRECT_I32) = range(9)
 REG_CLASSES = 11
 MLP_PARAMS = 4737
 
@@ -78,6 +79,7 @@ _SIGS = {
     "pgk_select_case_regs": (_i, [ctypes.POINTER(Machine), ctypes.POINTER(ctypes.c_int), _i, _i, _i,
                                   _i, ctypes.POINTER(Params), ctypes.POINTER(Case)]),
     "pgk_gemm": (_i, [_i, _i, _i, _i, _p, _i, _p, _i, _p, _i, _i, ctypes.POINTER(Params), _p]),
+    "pgk_gemm_i32": (_i, [_i, _i, _i, _p, _i, _p, _i, _p, _i, _i, ctypes.POINTER(Params), _p]),
     "pgk_gemm_case": (_i, [ctypes.POINTER(Case), _i, _i, _i, _p, _i, _p, _i, _p, _i, _i, _p]),
     "pgk_gemm_grouped": (_i, [_i, ctypes.POINTER(Problem), _i, ctypes.POINTER(Params), _i, _i, _p]),
     "pgk_cvt_bf16": (_i, [_i, _i, _p, _i, _p, _i, _i, _p]),
@@ -203,6 +205,16 @@ def gemm(A, B, C, dtype=F32, prog: Params | None = None, beta=0, stream=None, M=
     st = lib().pgk_gemm(M, N, K, dtype, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, int(beta),
                         ctypes.byref(prog) if prog is not None else None, _stream(stream))
     _check(st, "pgk_gemm")
+
+
+def gemm_i32(A, B, C, prog: Params | None = None, beta=0, stream=None):
+    """int32 GEMM modulo 2^32 (torch.int32 device tensors)."""
+    M, K = A.shape
+    N = B.shape[1]
+    st = lib().pgk_gemm_i32(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C), C.stride(0),
+                            int(beta), ctypes.byref(prog) if prog is not None else None,
+                            _stream(stream))
+    _check(st, "pgk_gemm_i32")
 
 
 def gemm_case(case: Case, A, B, C, beta=0, stream=None):

@@ -77,3 +77,30 @@ def test_rel_frobenius_closed_forms(oracle_mod):
     assert oracle_mod.rel_frobenius(X, X) == 0.0
     assert abs(oracle_mod.rel_frobenius(2 * X, X) - 1.0) < 1e-15
     assert abs(oracle_mod.rel_frobenius(np.zeros_like(X), X) - 1.0) < 1e-15
+
+
+def _wrap32(x):
+    x %= 2 ** 32
+    return x - 2 ** 32 if x >= 2 ** 31 else x
+
+
+def test_int32_oracle_against_python_integers(oracle_mod):
+    # full-range int32 values: products and sums overflow, exact Python integers
+    # reduced modulo 2^32 give the two's-complement result
+    rng = np.random.default_rng(11)
+    A = rng.integers(-2 ** 31, 2 ** 31, size=(5, 9), dtype=np.int64).astype(np.int32)
+    B = rng.integers(-2 ** 31, 2 ** 31, size=(9, 4), dtype=np.int64).astype(np.int32)
+    C0 = rng.integers(-2 ** 31, 2 ** 31, size=(5, 4), dtype=np.int64).astype(np.int32)
+    C = oracle_mod.gemm_i32(A, B)
+    C1 = oracle_mod.gemm_i32(A, B, C0=C0, beta=1)
+    for i in range(5):
+        for j in range(4):
+            exact = sum(int(A[i, k]) * int(B[k, j]) for k in range(9))
+            assert C[i, j] == _wrap32(exact)
+            assert C1[i, j] == _wrap32(exact + int(C0[i, j]))
+
+
+def test_int32_oracle_small_values_match_float_oracle(oracle_mod):
+    A, B = inputs.gemm_operands(17, 13, 29, seed=3, dist="integers")
+    Ci = oracle_mod.gemm_i32(A.astype(np.int32), B.astype(np.int32))
+    assert np.array_equal(Ci.astype(np.float64), oracle_mod.gemm(A, B))
