@@ -112,7 +112,11 @@ typedef enum {
     PGK_FAM_TC_FP8 = 5,   /* tcgen05 kind::f8f6f4, per-tile scaled E4M3           */
     PGK_FAM_PAPER_I32 = 6,  /* the paper family on int32                          */
     PGK_FAM_RB_I32 = 7,     /* the register-blocked family on int32               */
-    PGK_FAM_DIRECT_I32 = 8  /* the no-shared-memory leaf on int32                 */
+    PGK_FAM_DIRECT_I32 = 8, /* the no-shared-memory leaf on int32                 */
+    PGK_FAM_TRANSPOSE = 9,        /* transposition through shared memory (Fig. "transpose") */
+    PGK_FAM_TRANSPOSE_DIRECT = 10, /* transposition without shared memory                 */
+    PGK_FAM_JACOBI = 11,          /* 1D Jacobi step through shared memory (Fig. "1dj")    */
+    PGK_FAM_JACOBI_DIRECT = 12    /* 1D Jacobi step without shared memory                 */
 } pgk_family;
 
 /* A leaf chosen by the case discussion: the variant to launch and the values of
@@ -229,6 +233,52 @@ PGK_API pgk_status pgk_gemm_case(const pgk_case* c, int M, int N, int K, const f
  * CUDA, NO_MEMORY. */
 PGK_API pgk_status pgk_gemm_grouped(int G, const pgk_problem* problems, pgk_dtype dtype,
                             const pgk_params* prog, int use_graph, int beta, void* stream);
+
+/* ------------------------------------- the paper's other two parametric kernels */
+
+/* Number of register classes of a transposition / Jacobi register table:
+ * [0..3] the shared-memory variant with s = 1, 2, 4, 8; [4] the direct variant. */
+#define PGK_STENCIL_REG_CLASSES 5
+
+/* Case discussion of the parametric matrix transposition (Section 5, Fig.
+ * "transpose"): counters threads = B0*B1 <= T, registers, register file, shared
+ * memory 4*B0*(B1*s + 1) bytes (the a tile, padded) <= Z_B; leaves (4a,3a),
+ * (3b,4a) and (3b,4b).  prog: B0 x B1 thread block, s = columns per thread
+ * (1, 2, 4, 8).  regs_by_class: host array of PGK_STENCIL_REG_CLASSES ints, or
+ * NULL to read the compiled variants (needs a GPU).
+ * Errors: INVALID_ARG, INFEASIBLE, UNSUPPORTED, CUDA. */
+PGK_API pgk_status pgk_select_case_transpose(const pgk_machine* machine, const int* regs_by_class,
+                                             int rows, int cols, const pgk_params* prog,
+                                             pgk_case* out);
+
+/* dst = src^T on 32-bit words: src rows x cols (lds >= cols), dst cols x rows
+ * (ldd >= rows), device pointers.  prog NULL = (B0, B1, s) = (8, 32, 2), the
+ * paper's best block for order 2^14.  Errors: INVALID_ARG, INFEASIBLE,
+ * UNSUPPORTED, CUDA. */
+PGK_API pgk_status pgk_transpose(int rows, int cols, const void* src, int lds, void* dst, int ldd,
+                                 const pgk_params* prog, void* stream);
+
+/* Run the variant of a transposition case (any leaf).  Errors: INVALID_ARG, CUDA. */
+PGK_API pgk_status pgk_transpose_case(const pgk_case* c, int rows, int cols, const void* src,
+                                      int lds, void* dst, int ldd, void* stream);
+
+/* Case discussion of the 1D Jacobi step (Section 5, Fig. "1dj"): counters
+ * threads = B <= T, registers, register file, shared memory 4*(2*s*B + 2)
+ * bytes <= Z_B (the figure's 2sB + 2 words).  prog: B0 = B threads per block,
+ * s = points per thread (1, 2, 4, 8), B1 ignored.  Errors as for transposition. */
+PGK_API pgk_status pgk_select_case_jacobi(const pgk_machine* machine, const int* regs_by_class,
+                                          int n, const pgk_params* prog, pgk_case* out);
+
+/* `steps` time steps of 1D Jacobi on the int32 device array a[2n]: step t
+ * writes one half from the three-point average of the other (t odd: a[p+1] =
+ * (a[n+p] + a[n+p+1] + a[n+p+2]) / 3, else a[n+p+1] = (a[p] + a[p+1] + a[p+2])
+ * / 3) for every p in [0, n-2), C integer division.  One launch per step.
+ * prog NULL = (B, s) = (128, 2), the paper's best.  n >= 3.
+ * Errors: INVALID_ARG, INFEASIBLE, UNSUPPORTED, CUDA. */
+PGK_API pgk_status pgk_jacobi(int n, int steps, int32_t* a, const pgk_params* prog, void* stream);
+
+/* Run the variant of a Jacobi case (any leaf).  Errors: INVALID_ARG, CUDA. */
+PGK_API pgk_status pgk_jacobi_case(const pgk_case* c, int n, int steps, int32_t* a, void* stream);
 
 /* ------------------------------------------------ low-precision operands */
 

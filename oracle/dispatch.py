@@ -156,3 +156,63 @@ def brute_force(leaves, env):
         for idx in np.nonzero(ok)[0]:
             hits[idx].append(li)
     return hits
+
+
+# ----------------------------------------------- transposition and 1D Jacobi
+# The same counters and strategies for the paper's two other kernels, with the
+# shared-memory formulas of their GB300 variants:
+#   transposition: the a tile of B0 rows x (B1 s + 1) words, 4 B0 (B1 s + 1) bytes;
+#   Jacobi: read window s B + 2 words and s B results, 4 (2 s B + 2) bytes
+#   (Fig. "1dj" counts 2 s B + 2 words).
+# There is no register-capped build of these kernels, so strategy "1" leaves the
+# register count unchanged.
+
+def stencil_counters(kind, regs_of):
+    def ev_threads(prog):
+        if kind == "transpose":
+            return "B0 B1", lambda e: e["B0"] * e["B1"]
+        return "B", lambda e: e["B0"]
+
+    def ev_regs(prog):
+        return "regs", regs_of(prog)
+
+    def ev_regalloc(prog):
+        r = regs_of(prog)
+        th = ev_threads(prog)[1]
+
+        def v(e):
+            return (th(e) + 31) // 32 * (((r(e) * 32) + 255) // 256 * 256)
+        return "regalloc", v
+
+    def ev_smem(prog):
+        if not prog["cache"]:
+            return "0", lambda e: 0 * e["B0"]
+        if kind == "transpose":
+            if prog["s"] == "s":
+                return "4 B0 (B1 s + 1)", lambda e: 4 * e["B0"] * (e["B1"] * e["s"] + 1)
+            return "4 B0 (B1 + 1)", lambda e: 4 * e["B0"] * (e["B1"] + 1)
+        if prog["s"] == "s":
+            return "4 (2 s B + 2)", lambda e: 4 * (2 * e["s"] * e["B0"] + 2)
+        return "4 (2 B + 2)", lambda e: 4 * (2 * e["B0"] + 2)
+
+    return {
+        "r_threads": co.Counter("r_threads", "resource", "T", ev_threads, ()),
+        "r_regs": co.Counter("r_regs", "resource", "R", ev_regs, ("1",)),
+        "r_regalloc": co.Counter("r_regalloc", "resource", "RB", ev_regalloc, ("1",)),
+        "r_smem": co.Counter("r_smem", "resource", "ZB", ev_smem, ("3b", "4b")),
+    }
+
+
+STENCIL_STRATEGIES = {
+    "1": co.Strategy("1", True, lambda p: dict(p, regopt=True)),
+    "3b": co.Strategy("3b", False, lambda p: dict(p, s=1)),
+    "4b": co.Strategy("4b", False, lambda p: dict(p, cache=False)),
+}
+
+
+def stencil_case_tree(kind, regs_of, box):
+    Q = co.initial_quintuple({"cache": True, "s": "s", "regopt": False}, STRATEGY_ORDER,
+                             ["r_threads", "r_regs", "r_regalloc", "r_smem"],
+                             [co.Constraint("B0, B1, s >= 1",
+                                            lambda e: (e["B0"] >= 1) & (e["B1"] >= 1) & (e["s"] >= 1))])
+    return co.comprehensive_optimization(Q, stencil_counters(kind, regs_of), STENCIL_STRATEGIES, box)

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "case_walk.cuh"
 #include "pgk_internal.cuh"
 
 namespace pgk {
@@ -89,6 +90,7 @@ std::vector<Variant>& registry() {
     if (!g_registry_init) {
         register_simt_variants(g_registry);
         register_tc_variants(g_registry);
+        register_stencil_variants(g_registry);
         g_registry_init = true;
     }
     return g_registry;
@@ -122,7 +124,7 @@ int find_rb_variant(int family, int B0, int B1, int sr, int s, int tile) {
 
 // Registers per thread of variant `id` on the current device: the evaluation
 // function f_regs of step S2 (Section 1), read from the compiled code.
-static pgk_status variant_attrs(int id, int* regs, int* maxthr) {
+pgk_status variant_attrs(int id, int* regs, int* maxthr) {
     std::vector<Variant>& r = registry();
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -160,117 +162,93 @@ long long smem_rb(int B0, int B1, int sr, int s, int BK) {
 }
 
 // -------------------------------------------------------- case discussion
-// Program state of Algorithm 2 for the GEMM family.
-struct Prog {
-    int family;  // PGK_FAM_PAPER / RB / DIRECT (logical family; int32 mapped by is_int)
-    int is_int;  // int32 variants (PGK_I32)
-    int cache;   // (4a) / (4b)
-    int s, sr;   // effective granularity
-    int regopt;  // strategy "1" applied
-    int gran;    // strategy "3b" applied
-};
-
-enum { C_THREADS = 0, C_REGS = 1, C_REGALLOC = 2, C_SMEM = 3, N_COUNTERS = 4 };
-enum { O_REG = 0, O_GRAN = 1, O_NOCACHE = 2, N_STRATEGIES = 3 };
-
-// sigma(r_i): the strategies that may reduce each counter.
-static bool in_sigma(int counter, int strategy) {
-    switch (counter) {
-        case C_REGS:
-        case C_REGALLOC: return strategy == O_REG;
-        case C_SMEM: return strategy == O_GRAN || strategy == O_NOCACHE;
-        default: return false;
-    }
-}
-
-static void apply_strategy(int o, Prog& p) {
-    if (o == O_REG) {
-        p.regopt = 1;
-    } else if (o == O_GRAN) {
-        p.s = 1;
-        p.sr = 1;
-        p.gran = 1;
-        if (p.family == PGK_FAM_RB) p.family = PGK_FAM_PAPER;
-    } else {
-        p.cache = 0;
-        p.family = PGK_FAM_DIRECT;
-    }
-}
-
+// The GEMM family's program state and evaluation functions for walk_cases
+// (case_walk.cuh): families paper / register-blocked / direct, FP32 or int32.
 struct RegSource {
     const int* table;  // PGK_REG_CLASSES entries, or NULL = query the device
 };
 
-static int variant_of(const Prog& p, int B0, int B1, int BK) {
-    if (p.family == PGK_FAM_DIRECT)
-        return find_direct_variant(p.is_int ? PGK_FAM_DIRECT_I32 : PGK_FAM_DIRECT, p.regopt);
-    if (p.family == PGK_FAM_PAPER)
-        return find_paper_variant(p.is_int ? PGK_FAM_PAPER_I32 : PGK_FAM_PAPER, p.s, p.regopt);
-    return find_rb_variant(p.is_int ? PGK_FAM_RB_I32 : PGK_FAM_RB, B0, B1, p.sr, p.s, BK);
-}
+struct GemmSpec {
+    struct Prog {
+        int family;  // PGK_FAM_PAPER / RB / DIRECT (logical family; int32 mapped by is_int)
+        int is_int;  // int32 variants (PGK_I32)
+        int cache;   // (4a) / (4b)
+        int s, sr;   // effective granularity
+        int regopt;  // strategy "1" applied
+        int gran;    // strategy "3b" applied
+    };
+    int B0, B1, BK;
+    RegSource src;
 
-static pgk_status regs_of(const Prog& p, int B0, int B1, int BK, const RegSource& src, long long* out) {
-    if (src.table) {
-        int cls;
-        if (p.family == PGK_FAM_PAPER) {
-            const int si = p.s == 1 ? 0 : p.s == 2 ? 1 : p.s == 4 ? 2 : 3;
-            cls = si + (p.regopt ? 4 : 0);
-        } else if (p.family == PGK_FAM_DIRECT) {
-            cls = p.regopt ? 9 : 8;
-        } else {
-            cls = 10;
+    int variant_of(const Prog& p) const {
+        if (p.family == PGK_FAM_DIRECT)
+            return find_direct_variant(p.is_int ? PGK_FAM_DIRECT_I32 : PGK_FAM_DIRECT, p.regopt);
+        if (p.family == PGK_FAM_PAPER)
+            return find_paper_variant(p.is_int ? PGK_FAM_PAPER_I32 : PGK_FAM_PAPER, p.s, p.regopt);
+        return find_rb_variant(p.is_int ? PGK_FAM_RB_I32 : PGK_FAM_RB, B0, B1, p.sr, p.s, BK);
+    }
+
+    pgk_status regs_of(const Prog& p, long long* out) const {
+        if (src.table) {
+            int cls;
+            if (p.family == PGK_FAM_PAPER) {
+                const int si = p.s == 1 ? 0 : p.s == 2 ? 1 : p.s == 4 ? 2 : 3;
+                cls = si + (p.regopt ? 4 : 0);
+            } else if (p.family == PGK_FAM_DIRECT) {
+                cls = p.regopt ? 9 : 8;
+            } else {
+                cls = 10;
+            }
+            *out = src.table[cls];
+            return PGK_OK;
         }
-        *out = src.table[cls];
+        const int id = variant_of(p);
+        if (id < 0) {
+            set_error("no compiled variant for family %d s=%d sr=%d", p.family, p.s, p.sr);
+            return PGK_ERR_UNSUPPORTED;
+        }
+        int regs = -1;
+        pgk_status st = variant_attrs(id, &regs, NULL);
+        if (st != PGK_OK) return st;
+        *out = regs;
         return PGK_OK;
     }
-    const int id = variant_of(p, B0, B1, BK);
-    if (id < 0) {
-        set_error("no compiled variant for family %d s=%d sr=%d", p.family, p.s, p.sr);
-        return PGK_ERR_UNSUPPORTED;
-    }
-    int regs = -1;
-    pgk_status st = variant_attrs(id, &regs, NULL);
-    if (st != PGK_OK) return st;
-    *out = regs;
-    return PGK_OK;
-}
 
-static pgk_status eval_counter(int c, const Prog& p, int B0, int B1, int BK, const RegSource& src,
-                               long long* v) {
-    const long long threads = (long long)B0 * B1;
-    switch (c) {
-        case C_THREADS: *v = threads; return PGK_OK;
-        case C_REGS: return regs_of(p, B0, B1, BK, src, v);
-        case C_REGALLOC: {
-            long long r = 0;
-            pgk_status st = regs_of(p, B0, B1, BK, src, &r);
-            if (st != PGK_OK) return st;
-            const long long warps = (threads + 31) / 32;
-            *v = warps * (((r * 32) + 255) / 256 * 256);
-            return PGK_OK;
+    pgk_status eval(int c, const Prog& p, long long* v) const {
+        const long long threads = (long long)B0 * B1;
+        switch (c) {
+            case C_THREADS: *v = threads; return PGK_OK;
+            case C_REGS: return regs_of(p, v);
+            case C_REGALLOC: {
+                long long r = 0;
+                pgk_status st = regs_of(p, &r);
+                if (st != PGK_OK) return st;
+                *v = regalloc_bytes(threads, r);
+                return PGK_OK;
+            }
+            default:
+                if (!p.cache || p.family == PGK_FAM_DIRECT) *v = 0;
+                else if (p.family == PGK_FAM_PAPER) *v = smem_paper(B0, B1, p.s, BK);
+                else *v = smem_rb(B0, B1, p.sr, p.s, BK);
+                return PGK_OK;
         }
-        default:
-            if (!p.cache || p.family == PGK_FAM_DIRECT) *v = 0;
-            else if (p.family == PGK_FAM_PAPER) *v = smem_paper(B0, B1, p.s, BK);
-            else *v = smem_rb(B0, B1, p.sr, p.s, BK);
-            return PGK_OK;
     }
-}
 
-static long long limit_of(int c, const pgk_machine& m) {
-    switch (c) {
-        case C_THREADS: return m.max_threads_per_block;
-        case C_REGS: return m.max_regs_per_thread;
-        case C_REGALLOC: return m.regs_per_block;
-        default: return m.smem_per_block_optin;
+    void apply(int o, Prog& p) const {
+        if (o == O_REG) {
+            p.regopt = 1;
+        } else if (o == O_GRAN) {
+            p.s = 1;
+            p.sr = 1;
+            p.gran = 1;
+            if (p.family == PGK_FAM_RB) p.family = PGK_FAM_PAPER;
+        } else {
+            p.cache = 0;
+            p.family = PGK_FAM_DIRECT;
+        }
     }
-}
+};
 
-// Follows, at one concrete point, the branch of the case tree whose constraint
-// holds: accept (0 <= v <= R_i) continues with the next counter; refuse applies
-// the first remaining strategy of sigma(r_i) in the order 1, 3b, 4b, then pushes
-// r_1..r_i back on the counter stack (top = r_i, Remark "stacks"); with no such
-// strategy the branch is dropped and the point has no case (INFEASIBLE).
 static pgk_status simt_case(const pgk_machine* m, const RegSource& src, const pgk_params* prog,
                             int is_int, pgk_case* out) {
     const int B0 = prog->B0, B1 = prog->B1, s = prog->s;
@@ -285,7 +263,12 @@ static pgk_status simt_case(const pgk_machine* m, const RegSource& src, const pg
         set_error("precondition B0 <= B1*s fails (B0=%d B1=%d s=%d)", B0, B1, s);
         return PGK_ERR_INFEASIBLE;
     }
-    Prog p;
+    GemmSpec spec;
+    spec.B0 = B0;
+    spec.B1 = B1;
+    spec.BK = BK;
+    spec.src = src;
+    GemmSpec::Prog p;
     p.family = sr == 1 ? PGK_FAM_PAPER : PGK_FAM_RB;
     p.is_int = is_int;
     p.cache = 1;
@@ -303,38 +286,8 @@ static pgk_status simt_case(const pgk_machine* m, const RegSource& src, const pg
                   B1, sr, s, BK);
         return PGK_ERR_UNSUPPORTED;
     }
-    bool omega[N_STRATEGIES] = {true, true, true};
-    int gamma[64];
-    int top = 0;
-    for (int c = N_COUNTERS - 1; c >= 0; --c) gamma[top++] = c;  // r_1 on top
-    int guard = 0;
-    while (top > 0) {
-        if (++guard > 1000) {
-            set_error("case walk did not terminate");
-            return PGK_ERR_INFEASIBLE;
-        }
-        const int c = gamma[--top];
-        long long v = 0;
-        pgk_status st = eval_counter(c, p, B0, B1, BK, src, &v);
-        if (st != PGK_OK) return st;
-        if (v >= 0 && v <= limit_of(c, *m)) continue;  // accept branch
-        int chosen = -1;
-        for (int o = 0; o < N_STRATEGIES; ++o)
-            if (omega[o] && in_sigma(c, o)) {
-                chosen = o;
-                break;
-            }
-        if (chosen < 0) {
-            static const char* names[] = {"threads per block", "registers per thread",
-                                          "register file per block", "shared memory per block"};
-            set_error("no case: %s = %lld exceeds %lld and no strategy is left", names[c], v,
-                      limit_of(c, *m));
-            return PGK_ERR_INFEASIBLE;
-        }
-        apply_strategy(chosen, p);
-        omega[chosen] = false;
-        for (int r = 0; r <= c; ++r) gamma[top++] = r;  // push r_1..r_i: r_i ends on top
-    }
+    pgk_status st = walk_cases(*m, spec, p);
+    if (st != PGK_OK) return st;
     pgk_case cs;
     memset(&cs, 0, sizeof(cs));
     cs.leaf = !p.cache ? PGK_LEAF_3B4B : (p.gran ? PGK_LEAF_3B4A : PGK_LEAF_4A3A);
@@ -343,10 +296,10 @@ static pgk_status simt_case(const pgk_machine* m, const RegSource& src, const pg
                                                      : p.family == PGK_FAM_RB ? PGK_FAM_RB_I32
                                                                               : PGK_FAM_DIRECT_I32);
     cs.regopt = p.regopt;
-    cs.variant_id = variant_of(p, B0, B1, BK);
+    cs.variant_id = spec.variant_of(p);
     long long sm = 0, rg = 0;
-    eval_counter(C_SMEM, p, B0, B1, BK, src, &sm);
-    eval_counter(C_REGS, p, B0, B1, BK, src, &rg);
+    spec.eval(C_SMEM, p, &sm);
+    spec.eval(C_REGS, p, &rg);
     cs.smem_bytes = (int)sm;
     cs.regs = (int)rg;
     cs.threads = B0 * B1;

@@ -50,6 +50,7 @@ struct Variant {
 // Registration hooks, one per translation unit that defines variants.
 void register_simt_variants(std::vector<Variant>& v);
 void register_tc_variants(std::vector<Variant>& v);
+void register_stencil_variants(std::vector<Variant>& v);
 
 // Registry access (host.cu).
 std::vector<Variant>& registry();
@@ -58,6 +59,8 @@ int find_direct_variant(int family, int regopt);
 int find_rb_variant(int family, int B0, int B1, int sr, int s, int tile);
 // Register count of a variant on the current device (-1 if unavailable).
 int variant_regs(int id);
+// Registers per thread and max threads per block of a variant (cudaFuncGetAttributes, cached).
+pgk_status variant_attrs(int id, int* regs, int* maxthr);
 
 // Shared-memory formulas (bytes) of the SIMT families: the f_smem evaluation.
 long long smem_paper(int B0, int B1, int s, int BK);

@@ -455,7 +455,15 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 for (int j = 0; j < ncol; ++j) accr[j] = 0.f;
                 const int ksa = (p.K + 127) / 128, nsb = (p.N + 127) / 128;
                 const int nchunks = (nkb + Cfg::CHUNK - 1) / Cfg::CHUNK;
+                // FP8: the scales of chunk ch + 1 are fetched while chunk ch is waited
+                // for and folded, keeping the global-load latency off that path
+                auto chunk_scale = [&](int c) {
+                    return __ldg(p.sA + (size_t)tm * ksa + c) * __ldg(p.sB + (size_t)c * nsb + n0 / 128);
+                };
+                float sc_next = Cfg::MODE == MODE_FP8 ? chunk_scale(0) : 1.f;
                 for (int ch = 0; ch < nchunks; ++ch) {
+                    const float sc = sc_next;
+                    if (Cfg::MODE == MODE_FP8 && ch + 1 < nchunks) sc_next = chunk_scale(ch + 1);
                     int w = 1;
                     if (lane == 0)
                         w = mbar_wait(&accf_bar[acc], acc_phase, abort_flag, p.err,
@@ -469,10 +477,6 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     }
                     tc_fence_after();
                     // chunk sum times sA * sB (FP8: the tile scales of this 128-deep chunk)
-                    const float sc = Cfg::MODE == MODE_FP8
-                                         ? __ldg(p.sA + (size_t)tm * ksa + ch) *
-                                               __ldg(p.sB + (size_t)ch * nsb + n0 / 128)
-                                         : 1.f;
                     // loads issued per wait: both of a 64-column slice, else 32 columns
                     // at a time (128-column slices keep 128 accumulators in registers)
                     constexpr int NB = Cfg::BN / (Cfg::EPI_WARPS / 4) == 64 ? 2 : 1;

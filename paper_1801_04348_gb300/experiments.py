@@ -12,6 +12,8 @@ grouped    512 FP32 GEMMs, M, N, K log-uniform in [32, 2048] (multiples of 16, s
            replay, tile variant from pgk_autotune_grouped) against 512 separate pgk_gemm
            launches (eager and captured in one CUDA graph).
 mm         the paper's Table "mm" grid on GB300: int32, n = 2^10 and 2^11, (ub1, B0) x s.
+transpose  the paper's transposition grid at order 2^14 (GB/s).
+jacobi     the paper's 1D Jacobi grid (T = 4, length 2^15 + 2; and 2^27 + 2).
 precision  8192^3, normal(0,1) and row-scaled by 10^uniform(-3,3): every form's step
            time (FP32 in/out, preparation included), kernel time on prepared operands,
            and relative Frobenius error on 64 sampled rows against the FP64 oracle.
@@ -250,6 +252,49 @@ def mm_table(dev, stream):
     return {"config": "Table mm counterpart, int32", "sizes": out}
 
 
+def transpose_table(dev, stream):
+    """GB300 counterpart of the paper's transposition table: order 2^14 on 32-bit
+    words, (B0, B1) in {(4,32), (8,32), (16,32), (32,32)} x granularity {2, 4, 8};
+    time and GB/s of compulsory traffic (read a, write c: 2 x 4 n^2 bytes)."""
+    import torch
+    n = 16384
+    a = torch.randint(-2 ** 31, 2 ** 31 - 1, (n, n), dtype=torch.int32, device=dev)
+    c = torch.empty(n, n, dtype=torch.int32, device=dev)
+    sh = stream.cuda_stream
+    rows = []
+    for b0, b1 in ((4, 32), (8, 32), (16, 32), (32, 32)):
+        for s in (2, 4, 8):
+            p = pgk.params(b0, b1, s)
+            run = lambda: pgk.transpose(a, c, p, stream=sh)
+            run()
+            ms = _events_ms(run, 10, stream)
+            rows.append({"B0": b0, "B1": b1, "s": s, "ms": ms, "gbs": 8.0 * n * n / ms / 1e6})
+    best = min(rows, key=lambda r: r["ms"])
+    return {"config": "transposition order 2^14", "grid": rows, "best": best}
+
+
+def jacobi_table(dev, stream):
+    """GB300 counterpart of the paper's 1D Jacobi table: T = 4 steps on a vector of
+    length 2^15 + 2, blocks 16-256 x granularity {2, 4, 8}; and the same grid on
+    2^27 + 2 points, where the step is HBM-bound (4 + 4 bytes per point)."""
+    import torch
+    out = {}
+    sh = stream.cuda_stream
+    for n, steps in ((2 ** 15 + 2, 4), (2 ** 27 + 2, 4)):
+        a = torch.randint(-2 ** 20, 2 ** 20, (2 * n,), dtype=torch.int32, device=dev)
+        rows = []
+        for b in (16, 32, 64, 128, 256):
+            for s in (2, 4, 8):
+                p = pgk.params(b, 1, s)
+                run = lambda: pgk.jacobi(a, n, steps, p, stream=sh)
+                run()
+                ms = _events_ms(run, 10, stream)
+                rows.append({"B": b, "s": s, "ms": ms, "ms_per_step": ms / steps,
+                             "gbs": 8.0 * (n - 2) * steps / ms / 1e6})
+        out[str(n)] = {"grid": rows, "best": min(rows, key=lambda r: r["ms"])}
+    return {"config": "1D Jacobi", "sizes": out}
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
@@ -261,7 +306,7 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
     fns = {"config1": config1, "scale": scale, "grouped": grouped, "precision": precision,
-           "mm": mm_table}
+           "mm": mm_table, "transpose": transpose_table, "jacobi": jacobi_table}
     for w in args.which:
         t0 = time.time()
         with torch.cuda.stream(stream):

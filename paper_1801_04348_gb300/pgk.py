@@ -21,7 +21,8 @@ F32, BF16, FP8_E4M3, SPLIT_BF16, I32 = 0, 1, 2, 3, 4
 DTYPES = {"f32": F32, "bf16": BF16, "fp8": FP8_E4M3, "split": SPLIT_BF16, "i32": I32}
 LEAF_4A3A, LEAF_3B4A, LEAF_3B4B = 0, 1, 2
 (FAM_PAPER, FAM_RB, FAM_DIRECT, FAM_TC_BF16, FAM_TC_SPLIT, FAM_TC_FP8, FAM_PAPER_I32, FAM_RB_I32,
- FAM_DIRECT_I32) = range(9)
+ FAM_DIRECT_I32, FAM_TRANSPOSE, FAM_TRANSPOSE_DIRECT, FAM_JACOBI, FAM_JACOBI_DIRECT) = range(13)
+STENCIL_REG_CLASSES = 5
 REG_CLASSES = 11
 MLP_PARAMS = 4737
 
@@ -82,6 +83,14 @@ _SIGS = {
     "pgk_gemm_i32": (_i, [_i, _i, _i, _p, _i, _p, _i, _p, _i, _i, ctypes.POINTER(Params), _p]),
     "pgk_gemm_case": (_i, [ctypes.POINTER(Case), _i, _i, _i, _p, _i, _p, _i, _p, _i, _i, _p]),
     "pgk_gemm_grouped": (_i, [_i, ctypes.POINTER(Problem), _i, ctypes.POINTER(Params), _i, _i, _p]),
+    "pgk_select_case_transpose": (_i, [ctypes.POINTER(Machine), ctypes.POINTER(ctypes.c_int), _i, _i,
+                                       ctypes.POINTER(Params), ctypes.POINTER(Case)]),
+    "pgk_transpose": (_i, [_i, _i, _p, _i, _p, _i, ctypes.POINTER(Params), _p]),
+    "pgk_transpose_case": (_i, [ctypes.POINTER(Case), _i, _i, _p, _i, _p, _i, _p]),
+    "pgk_select_case_jacobi": (_i, [ctypes.POINTER(Machine), ctypes.POINTER(ctypes.c_int), _i,
+                                    ctypes.POINTER(Params), ctypes.POINTER(Case)]),
+    "pgk_jacobi": (_i, [_i, _i, _p, ctypes.POINTER(Params), _p]),
+    "pgk_jacobi_case": (_i, [ctypes.POINTER(Case), _i, _i, _p, _p]),
     "pgk_cvt_bf16": (_i, [_i, _i, _p, _i, _p, _i, _i, _p]),
     "pgk_split_bf16": (_i, [_i, _i, _p, _i, _p, _p, _i, _i, _p]),
     "pgk_quant_fp8": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _i, _p]),
@@ -258,6 +267,47 @@ def autotune_grouped(problems, candidates=None, reps=3, stream=None):
     _check(lib().pgk_autotune_grouped(len(problems), problems, arr, len(cand), reps, ms,
                                       ctypes.byref(best), _stream(stream)), "pgk_autotune_grouped")
     return best, [(cand[i], ms[i]) for i in range(len(cand))]
+
+
+# ------------------------------------------- transposition and 1D Jacobi
+def select_case_transpose(machine: Machine, rows, cols, prog: Params, regs=None):
+    """Returns (status, Case); regs = 5 register counts or None (query the GPU)."""
+    arr = (ctypes.c_int * STENCIL_REG_CLASSES)(*regs) if regs is not None else None
+    c = Case()
+    st = lib().pgk_select_case_transpose(ctypes.byref(machine), arr, rows, cols, ctypes.byref(prog),
+                                         ctypes.byref(c))
+    return st, c
+
+
+def transpose(src, dst, prog: Params | None = None, stream=None):
+    rows, cols = src.shape
+    _check(lib().pgk_transpose(rows, cols, _ptr(src), src.stride(0), _ptr(dst), dst.stride(0),
+                               ctypes.byref(prog) if prog is not None else None, _stream(stream)),
+           "pgk_transpose")
+
+
+def transpose_case(case: Case, src, dst, stream=None):
+    rows, cols = src.shape
+    _check(lib().pgk_transpose_case(ctypes.byref(case), rows, cols, _ptr(src), src.stride(0), _ptr(dst),
+                                    dst.stride(0), _stream(stream)), "pgk_transpose_case")
+
+
+def select_case_jacobi(machine: Machine, n, prog: Params, regs=None):
+    arr = (ctypes.c_int * STENCIL_REG_CLASSES)(*regs) if regs is not None else None
+    c = Case()
+    st = lib().pgk_select_case_jacobi(ctypes.byref(machine), arr, n, ctypes.byref(prog), ctypes.byref(c))
+    return st, c
+
+
+def jacobi(a, n, steps, prog: Params | None = None, stream=None):
+    """a: int32 device tensor of 2n entries, updated in place."""
+    _check(lib().pgk_jacobi(n, steps, _ptr(a), ctypes.byref(prog) if prog is not None else None,
+                            _stream(stream)), "pgk_jacobi")
+
+
+def jacobi_case(case: Case, a, n, steps, stream=None):
+    _check(lib().pgk_jacobi_case(ctypes.byref(case), n, steps, _ptr(a), _stream(stream)),
+           "pgk_jacobi_case")
 
 
 # --------------------------------------------------------- low precision
