@@ -416,6 +416,13 @@ PGK_API pgk_status pgk_tune_cache_load(const char* path);
  * the current device).  Returns OK, TIMEOUT, or CUDA. */
 PGK_API pgk_status pgk_check_device_error(void);
 
+/* Exercises the bounded device wait the tensor-core kernels use: one thread
+ * waits on an mbarrier that nothing arrives at, gives up after limit_ns
+ * (at most 2 s), sets the device error word and returns normally; the next
+ * pgk_check_device_error() reports PGK_ERR_TIMEOUT and the context stays
+ * usable.  No fault, trap or hang is involved.  Errors: INVALID_ARG, CUDA. */
+PGK_API pgk_status pgk_selftest_bounded_wait(unsigned long long limit_ns, void* stream);
+
 PGK_API const char* pgk_status_string(pgk_status s);
 /* Message for the last failing call on this host thread ("" if none). */
 PGK_API const char* pgk_last_error(void);

@@ -38,6 +38,7 @@ static constexpr unsigned int ERR_TIMEOUT_PRODUCER = 0x1u;
 static constexpr unsigned int ERR_TIMEOUT_MMA = 0x2u;
 static constexpr unsigned int ERR_TIMEOUT_EPILOGUE = 0x4u;
 static constexpr unsigned int ERR_TIMEOUT_DRAIN = 0x8u;
+static constexpr unsigned int ERR_TIMEOUT_SELFTEST = 0x10u;
 
 template <int MODE_, int BN_, int STAGES_>
 struct TcCfg {
@@ -108,14 +109,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // was aborted by another warp or the limit expired (then the abort flag and
 // the device error word are set).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          unsigned int* err, unsigned int code) {
+                                          unsigned int* err, unsigned int code,
+                                          unsigned long long limit_ns = WAIT_LIMIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 0) {
             if (*abort_flag) return false;
-            if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+            if (globaltimer() - t0 > limit_ns) {
                 *abort_flag = 1;
                 atomicOr(err, code);
                 return false;
@@ -587,6 +589,20 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
     }
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives at, with a short limit; the wait gives up, sets the error word and the
+// kernel returns normally.
+__global__ void k_wait_selftest(unsigned int* err, unsigned long long limit_ns) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_sh;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_wait(&bar, 0, &abort_sh, err, ERR_TIMEOUT_SELFTEST, limit_ns);
+    }
+}
+
 // ------------------------------------------------------------ host side
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 static std::mutex g_tc_mu;
@@ -868,4 +884,17 @@ extern "C" pgk_status pgk_gemm_lowp(int M, int N, int K, pgk_dtype dtype, const 
     if (st != PGK_OK) return st;
     return tc_gemm_launch(c, M, N, K, dtype, A, lda, Bt, ldbt, A_lo, Bt_lo, scaleA, scaleB, C, ldc,
                           beta, (cudaStream_t)stream);
+}
+
+extern "C" pgk_status pgk_selftest_bounded_wait(unsigned long long limit_ns, void* stream) {
+    if (limit_ns == 0 || limit_ns > 2000000000ULL) {
+        set_error("limit must be in (0, 2 s]");
+        return PGK_ERR_INVALID_ARG;
+    }
+    pgk_status st;
+    unsigned int* err = device_error_word(&st);
+    if (!err) return st;
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(err, limit_ns);
+    PGK_CUDA_TRY(cudaGetLastError(), "wait self-test launch");
+    return PGK_OK;
 }

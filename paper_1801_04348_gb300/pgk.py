@@ -112,6 +112,7 @@ _SIGS = {
     "pgk_tune_cache_save": (_i, [ctypes.c_char_p]),
     "pgk_tune_cache_load": (_i, [ctypes.c_char_p]),
     "pgk_check_device_error": (_i, []),
+    "pgk_selftest_bounded_wait": (_i, [ctypes.c_ulonglong, _p]),
     "pgk_shutdown": (_i, []),
 }
 
@@ -415,6 +416,10 @@ def tune_cache_load(path: str):
 
 def check_device_error():
     _check(lib().pgk_check_device_error(), "pgk_check_device_error")
+
+
+def selftest_bounded_wait(limit_ns=50_000_000, stream=None):
+    _check(lib().pgk_selftest_bounded_wait(int(limit_ns), _stream(stream)), "pgk_selftest_bounded_wait")
 
 
 def shutdown():
