@@ -403,6 +403,22 @@ PGK_API pgk_status pgk_autotune_grouped(int G, const pgk_problem* problems,
 /* Number of built-in candidates of a form (the autotuner's default set). */
 PGK_API int pgk_default_candidates(pgk_dtype dtype, pgk_params* out, int cap);
 
+/* Installs a trained cost model for the learned case selection of one form
+ * (PGK_F32, PGK_BF16, PGK_SPLIT_BF16 or PGK_FP8_E4M3): theta (host,
+ * PGK_MLP_PARAMS floats), the 7 feature means mu and scales sd (features:
+ * log2 M, log2 N, log2 K, log2 B0, log2 B1, log2 s, form code 0 FP32 paper-form,
+ * 1 FP32 register-blocked, 2 BF16, 3 split, 4 FP8), the target normalisation
+ * (tmu, tsd) of ln(milliseconds), and k.  Afterwards pgk_gemm(prog = NULL) on a
+ * shape missing from the tuning cache scores the form's candidate set with
+ * pgk_mlp_forward, times the k best predictions on the call's own operands
+ * (beta = 0; with beta = 1 the best prediction is taken untimed), stores the
+ * winner in the tuning cache and runs it.  That first call on a new shape
+ * synchronises its stream.  Errors: INVALID_ARG, CUDA. */
+PGK_API pgk_status pgk_costmodel_load(pgk_dtype dtype, const float* theta, const float* mu,
+                                      const float* sd, float tmu, float tsd, int k);
+/* Removes the cost model of a form (back to the untuned default on a miss). */
+PGK_API pgk_status pgk_costmodel_clear(pgk_dtype dtype);
+
 /* Store / look up the tuned parameters of (current device, M, N, K, dtype). */
 PGK_API pgk_status pgk_tune_cache_put(int M, int N, int K, pgk_dtype dtype, const pgk_params* p);
 PGK_API pgk_status pgk_tune_cache_get(int M, int N, int K, pgk_dtype dtype, pgk_params* p);

@@ -511,7 +511,9 @@ pgk_status pgk_gemm(int M, int N, int K, pgk_dtype dtype, const float* A, int ld
     pgk_params p;
     if (prog) {
         p = *prog;
-    } else if (pgk_tune_cache_get(M, N, K, dtype, &p) != PGK_OK) {
+    } else if (pgk_tune_cache_get(M, N, K, dtype, &p) != PGK_OK &&
+               learned_select(M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, (cudaStream_t)stream,
+                              &p) != PGK_OK) {
         p = default_params(M, N, K, dtype);
     }
     pgk_case c;
@@ -532,6 +534,7 @@ pgk_status pgk_gemm_i32(int M, int N, int K, const int32_t* A, int lda, const in
 }
 
 pgk_status pgk_shutdown(void) {
+    costmodel_release();
     grouped_release();
     tune_cache_release();
     free_workspaces();

@@ -156,11 +156,160 @@ static int tc_candidates(pgk_dtype dtype, pgk_params* out, int cap) {
     return n;
 }
 
+// ---------------------------------------------------- learned selection
+// A trained cost model per form: ranks the form's learned candidate set for a
+// new shape on the GPU (pgk_mlp_forward), the best k predictions are timed.
+struct CostModel {
+    bool on = false;
+    int k = 3;
+    float mu[7], sd[7];
+    float tmu = 0.f, tsd = 1.f;
+    float* d_theta = nullptr;  // device copy of the parameters
+};
+static CostModel g_cm[8];
+static std::mutex g_cm_mu;
+
+// The learned candidate set: the paper-form grid (B0, B1 in {8, 16, 32},
+// s in {1, 2, 4}, B0 <= B1 s, tile = B0) and the register-blocked variants with
+// sr = s and tile 8 (F32); the tensor-core candidates of the form otherwise.
+static std::vector<pgk_params> learned_candidates(pgk_dtype dtype) {
+    std::vector<pgk_params> c;
+    if (dtype == PGK_F32) {
+        const int bs[3] = {8, 16, 32}, ss[3] = {1, 2, 4};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                for (int s = 0; s < 3; ++s)
+                    if (bs[a] <= bs[b] * ss[s]) {
+                        pgk_params p = {bs[a], bs[b], ss[s], 1, 0};
+                        c.push_back(p);
+                    }
+        std::vector<Variant>& r = registry();
+        for (size_t i = 0; i < r.size(); ++i) {
+            const pgk_variant_info& v = r[i].info;
+            if (v.family == PGK_FAM_RB && v.sr == v.s && v.tile == 8) {
+                pgk_params p = {v.B0, v.B1, v.s, v.sr, v.tile};
+                c.push_back(p);
+            }
+        }
+    } else {
+        const int n = tc_candidates(dtype, NULL, 0);
+        c.resize(n);
+        tc_candidates(dtype, c.data(), n);
+    }
+    return c;
+}
+
+static float form_code(pgk_dtype dtype, const pgk_params& p) {
+    if (dtype == PGK_F32) return p.sr > 1 ? 1.f : 0.f;
+    return dtype == PGK_BF16 ? 2.f : dtype == PGK_SPLIT_BF16 ? 3.f : 4.f;
+}
+
+pgk_status learned_select(int M, int N, int K, pgk_dtype dtype, const float* A, int lda,
+                          const float* B, int ldb, float* C, int ldc, int beta,
+                          cudaStream_t stream, pgk_params* out) {
+    if (dtype < 0 || dtype >= 8) return PGK_ERR_INVALID_ARG;
+    CostModel cm;
+    {
+        std::lock_guard<std::mutex> lk(g_cm_mu);
+        if (!g_cm[dtype].on) return PGK_ERR_UNSUPPORTED;
+        cm = g_cm[dtype];
+    }
+    std::vector<pgk_params> cand = learned_candidates(dtype);
+    const int n = (int)cand.size();
+    if (n == 0) return PGK_ERR_UNSUPPORTED;
+    std::vector<float> X((size_t)n * 7), y(n);
+    for (int i = 0; i < n; ++i) {
+        const float f[7] = {log2f((float)M), log2f((float)N), log2f((float)K), log2f((float)cand[i].B0),
+                            log2f((float)cand[i].B1), log2f((float)cand[i].s), form_code(dtype, cand[i])};
+        for (int j = 0; j < 7; ++j) X[(size_t)i * 7 + j] = (f[j] - cm.mu[j]) / cm.sd[j];
+    }
+    pgk_status st;
+    float* dX = (float*)workspace(WS_COUNTER, sizeof(float) * (size_t)n * 8, &st);
+    if (!dX) return st;
+    float* dy = dX + (size_t)n * 7;
+    PGK_CUDA_TRY(cudaMemcpyAsync(dX, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, stream),
+                 "feature upload");
+    if ((st = pgk_mlp_forward(n, dX, cm.d_theta, dy, stream)) != PGK_OK) return st;
+    PGK_CUDA_TRY(cudaMemcpyAsync(y.data(), dy, sizeof(float) * n, cudaMemcpyDeviceToHost, stream),
+                 "prediction read");
+    PGK_CUDA_TRY(cudaStreamSynchronize(stream), "prediction sync");
+    // predicted ln(ms) is monotone in the network output: rank by the output
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return y[a] < y[b]; });
+    pgk_machine m;
+    if ((st = current_machine(&m, NULL)) != PGK_OK) return st;
+    std::vector<pgk_params> top;
+    for (int i = 0; i < n && (int)top.size() < std::max(1, cm.k); ++i) {
+        pgk_case c;
+        if (pgk_select_case(&m, M, N, K, dtype, &cand[order[i]], &c) == PGK_OK) top.push_back(cand[order[i]]);
+    }
+    if (top.empty()) return PGK_ERR_INFEASIBLE;
+    if (beta || top.size() == 1) {
+        *out = top[0];  // C must not be overwritten by trial runs: take the best prediction
+        return pgk_tune_cache_put(M, N, K, dtype, out);
+    }
+    pgk_params best;
+    st = pgk_autotune(M, N, K, dtype, A, lda, B, ldb, C, ldc, top.data(), (int)top.size(), 1, NULL,
+                      &best, NULL, stream);
+    if (st != PGK_OK) return st;
+    *out = best;
+    return PGK_OK;
+}
+
+void costmodel_release() {
+    std::lock_guard<std::mutex> lk(g_cm_mu);
+    for (int i = 0; i < 8; ++i) {
+        if (g_cm[i].d_theta) cudaFree(g_cm[i].d_theta);
+        g_cm[i] = CostModel();
+    }
+}
+
 }  // namespace pgk
 
 using namespace pgk;
 
 extern "C" {
+
+pgk_status pgk_costmodel_load(pgk_dtype dtype, const float* theta, const float* mu, const float* sd,
+                              float tmu, float tsd, int k) {
+    if ((int)dtype < 0 || (int)dtype >= 8 || !theta || !mu || !sd || !(tsd > 0.f) || k < 1) {
+        set_error("bad cost-model arguments");
+        return PGK_ERR_INVALID_ARG;
+    }
+    for (int j = 0; j < 7; ++j)
+        if (!(sd[j] > 0.f)) {
+            set_error("feature scales must be positive");
+            return PGK_ERR_INVALID_ARG;
+        }
+    std::lock_guard<std::mutex> lk(g_cm_mu);
+    CostModel& cm = g_cm[dtype];
+    if (!cm.d_theta) {
+        PGK_CUDA_TRY(cudaMalloc(&cm.d_theta, sizeof(float) * PGK_MLP_PARAMS), "cost-model allocation");
+    }
+    PGK_CUDA_TRY(cudaMemcpy(cm.d_theta, theta, sizeof(float) * PGK_MLP_PARAMS, cudaMemcpyHostToDevice),
+                 "cost-model upload");
+    for (int j = 0; j < 7; ++j) {
+        cm.mu[j] = mu[j];
+        cm.sd[j] = sd[j];
+    }
+    cm.tmu = tmu;
+    cm.tsd = tsd;
+    cm.k = k;
+    cm.on = true;
+    return PGK_OK;
+}
+
+pgk_status pgk_costmodel_clear(pgk_dtype dtype) {
+    if ((int)dtype < 0 || (int)dtype >= 8) {
+        set_error("bad dtype");
+        return PGK_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_cm_mu);
+    if (g_cm[dtype].d_theta) cudaFree(g_cm[dtype].d_theta);
+    g_cm[dtype] = CostModel();
+    return PGK_OK;
+}
 
 pgk_status pgk_tune_cache_put(int M, int N, int K, pgk_dtype dtype, const pgk_params* p) {
     if (!p) {

@@ -89,5 +89,10 @@ pgk_status tc_gemm_launch(const pgk_case& c, int M, int N, int K, pgk_dtype dtyp
 // ------------------------------------------------------------- grouped
 void grouped_release();
 void tune_cache_release();
+void costmodel_release();
+// Learned selection for pgk_gemm(prog = NULL) on a tuning-cache miss (misc.cu).
+pgk_status learned_select(int M, int N, int K, pgk_dtype dtype, const float* A, int lda,
+                          const float* B, int ldb, float* C, int ldc, int beta,
+                          cudaStream_t stream, pgk_params* out);
 
 }  // namespace pgk

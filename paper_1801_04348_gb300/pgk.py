@@ -107,6 +107,9 @@ _SIGS = {
     "pgk_grouped_variants": (_i, [ctypes.POINTER(Params), _i, ctypes.POINTER(ctypes.c_int)]),
     "pgk_autotune_grouped": (_i, [_i, ctypes.POINTER(Problem), ctypes.POINTER(Params), _i, _i,
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Params), _p]),
+    "pgk_costmodel_load": (_i, [_i, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                ctypes.POINTER(ctypes.c_float), _f, _f, _i]),
+    "pgk_costmodel_clear": (_i, [_i]),
     "pgk_tune_cache_put": (_i, [_i, _i, _i, _i, ctypes.POINTER(Params)]),
     "pgk_tune_cache_get": (_i, [_i, _i, _i, _i, ctypes.POINTER(Params)]),
     "pgk_tune_cache_save": (_i, [ctypes.c_char_p]),
@@ -394,6 +397,26 @@ def autotune(A, B, C, dtype=F32, candidates=None, reps=3, log_path=None, stream=
                             log_path.encode() if log_path else None, _stream(stream))
     _check(st, "pgk_autotune")
     return best, [(cand[i], ms[i]) for i in range(len(cand))]
+
+
+def costmodel_load(dtype, theta, mu, sd, tmu, tsd, k=3):
+    """Installs a trained cost model (host arrays) for pgk_gemm's learned selection."""
+    th = (ctypes.c_float * len(theta))(*[float(x) for x in theta])
+    m = (ctypes.c_float * 7)(*[float(x) for x in mu])
+    s = (ctypes.c_float * 7)(*[float(x) for x in sd])
+    _check(lib().pgk_costmodel_load(dtype, th, m, s, float(tmu), float(tsd), int(k)),
+           "pgk_costmodel_load")
+
+
+def costmodel_load_file(dtype, path, k=3):
+    import json
+    with open(path) as f:
+        d = json.load(f)
+    costmodel_load(dtype, d["theta"], d["mu"], d["sd"], d["tmu"], d["tsd"], k)
+
+
+def costmodel_clear(dtype):
+    _check(lib().pgk_costmodel_clear(dtype), "pgk_costmodel_clear")
 
 
 def tune_cache_put(M, N, K, dtype, p: Params):
