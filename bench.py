@@ -120,12 +120,13 @@ def cpu_baseline(M, N, K, seed, target_s=12.0):
     from paper_1801_04348_gb300 import inputs
     A, B = inputs.gemm_operands(M, N, K, seed=seed)
     oracle.build()
-    rows = np.arange(2, dtype=np.int64)
+    cores = oracle.max_threads()
+    # calibrate with one row per core (the oracle parallelises over rows)
+    rows = np.linspace(0, M - 1, cores).astype(np.int64)
     t0 = time.perf_counter()
     oracle.gemm(A, B, rows=rows)
-    t1 = time.perf_counter() - t0
-    cores = oracle.max_threads()
-    nrows = int(max(cores, min(M, round(target_s / max(t1 / 2, 1e-6)))))
+    per_row = (time.perf_counter() - t0) / cores
+    nrows = int(min(M, round(target_s / max(per_row, 1e-9))))
     nrows = max(cores, (nrows // cores) * cores)
     rows = np.linspace(0, M - 1, nrows).astype(np.int64)
     t0 = time.perf_counter()
