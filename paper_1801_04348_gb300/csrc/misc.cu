@@ -86,20 +86,34 @@ void free_workspaces() {
 static std::mutex g_tc_mu;
 static std::map<std::string, pgk_params> g_tune;
 
-static std::string tune_key(int M, int N, int K, pgk_dtype dtype) {
+// Device part of the cache key ("<name>_sm<cc>"), looked up once per device.
+static std::string device_tag() {
+    static std::mutex mu;
+    static std::string tags[64];
     int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceProp p;
-    char name[300] = "unknown";
-    if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) {
-        snprintf(name, sizeof(name), "%s_sm%d%d", p.name, p.major, p.minor);
-    } else {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
+        return "unknown";
     }
-    for (char* c = name; *c; ++c)
-        if (*c == ' ' || *c == '\t') *c = '_';
+    std::lock_guard<std::mutex> lk(mu);
+    if (tags[dev].empty()) {
+        cudaDeviceProp p;
+        char name[300] = "unknown";
+        if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) {
+            snprintf(name, sizeof(name), "%s_sm%d%d", p.name, p.major, p.minor);
+        } else {
+            cudaGetLastError();
+        }
+        for (char* c = name; *c; ++c)
+            if (*c == ' ' || *c == '\t') *c = '_';
+        tags[dev] = name;
+    }
+    return tags[dev];
+}
+
+static std::string tune_key(int M, int N, int K, pgk_dtype dtype) {
     char buf[512];
-    snprintf(buf, sizeof(buf), "%s %d %d %d %d", name, M, N, K, (int)dtype);
+    snprintf(buf, sizeof(buf), "%s %d %d %d %d", device_tag().c_str(), M, N, K, (int)dtype);
     return buf;
 }
 

@@ -69,7 +69,7 @@ long long smem_rb(int B0, int B1, int sr, int s, int BK);
 // ------------------------------------------------------------- workspace
 // Library-owned device memory, grown on demand, freed by pgk_shutdown().
 void* workspace(int slot, size_t bytes, pgk_status* st);
-enum { WS_A0 = 0, WS_A1, WS_B0, WS_B1, WS_SA, WS_SB, WS_TABLE, WS_COUNTER, WS_PARTIAL, WS_COUNT };
+enum { WS_A0 = 0, WS_A1, WS_B0, WS_B1, WS_SA, WS_SB, WS_TABLE, WS_COUNTER, WS_PARTIAL, WS_SPLITK, WS_COUNT };
 // Device error word set by bounded waits (tensor-core kernels).
 unsigned int* device_error_word(pgk_status* st);
 void free_workspaces();

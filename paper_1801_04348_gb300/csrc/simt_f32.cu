@@ -7,9 +7,14 @@
 //     run-time indexed register array would live in local memory).
 //     Leaves (4a,3a) and (3b,4a) of the case discussion.
 //   * "direct" family: no shared memory, one output per thread; leaf (3b,4b).
-//   * "rb" family: register-blocked sr x s micro tiles (simt_rb.cuh).
+//   * "rb" family: register-blocked sr x s micro tiles (simt_rb.cuh).  When the
+//     output has fewer tiles than SMs and K >= 4096 the launch splits K into
+//     slices (at least 1024 deep); slice partials land in a library workspace and
+//     a second kernel adds them in slice order.
 // Every variant handles arbitrary M, N, K >= 1 with predicated, zero-filled
 // tails (the paper's k loop drops the remainder of n / B0).
+#include <algorithm>
+
 #include "pgk_internal.cuh"
 #include "simt_rb.cuh"
 
@@ -146,11 +151,78 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) k_rb(SimtArgs p) {
                           reinterpret_cast<float*>(smem_rb4));
 }
 
+// Split-K: blockIdx.y selects a slice [y * kslice, (y + 1) * kslice) of K; the
+// tile's partial product goes to slice y of the workspace P (M x N each).
+template <class Cfg, bool INT>
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) k_rb_splitk(SimtArgs p, float* P, int kslice) {
+    extern __shared__ float4 smem_sk4[];
+    const int tiles_m = (p.M + Cfg::BM - 1) / Cfg::BM;
+    const int tiles_n = (p.N + Cfg::BN - 1) / Cfg::BN;
+    int bm, bn;
+    grouped_tile_coords(blockIdx.x, tiles_m, tiles_n, bm, bn);
+    const int k0 = blockIdx.y * kslice;
+    const int kn = min(kslice, p.K - k0);
+    float* Py = P + (size_t)blockIdx.y * p.M * p.N;
+    RbTile<Cfg, INT>::run(p.A + k0, p.lda, p.B + (size_t)k0 * p.ldb, p.ldb, Py, p.N, p.M, p.N, kn,
+                          bm * Cfg::BM, bn * Cfg::BN, 0, p.vecA, p.vecB, (p.N & 3) == 0,
+                          reinterpret_cast<float*>(smem_sk4));
+}
+
+// C = (beta ? C : 0) + sum over slices of P, slices added in order.
+template <bool INT>
+__global__ void k_splitk_reduce(SimtArgs p, const float* __restrict__ P, int splits) {
+    const long long total = (long long)p.M * p.N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / p.N), c = (int)(i - (long long)r * p.N);
+        float acc = P[i];
+        for (int y = 1; y < splits; ++y) acc = add32<INT>(acc, P[(size_t)y * total + i]);
+        float* cp = p.C + (size_t)r * p.ldc + c;
+        *cp = p.beta ? add32<INT>(*cp, acc) : acc;
+    }
+}
+
 template <class Cfg, bool INT>
 static cudaError_t launch_rb(const SimtArgs& p, int, cudaStream_t st) {
     const long long tiles =
         (long long)((p.M + Cfg::BM - 1) / Cfg::BM) * ((p.N + Cfg::BN - 1) / Cfg::BN);
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    // Fewer output tiles than the GPU holds resident blocks, on a long K: split K
+    // so that every SM is filled (slices of at least 1024, a multiple of BK).
+    pgk_machine m;
+    int splits = 1;
+    if (p.K >= 4096 && current_machine(&m, NULL) == PGK_OK) {
+        if (Cfg::SMEM > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute((const void*)k_rb_splitk<Cfg, INT>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 Cfg::SMEM);
+            if (e != cudaSuccess) return e;
+        }
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_rb_splitk<Cfg, INT>,
+                                                          Cfg::NT, Cfg::SMEM) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        const long long slots = (long long)std::max(per_sm, 1) * m.sm_count;
+        if (tiles < slots) {
+            splits = (int)std::min<long long>((slots + tiles - 1) / tiles, 16);
+            splits = std::min(splits, p.K / 1024);
+        }
+    }
+    if (splits >= 2) {
+        const int kslice = ((p.K + splits - 1) / splits + Cfg::BK - 1) / Cfg::BK * Cfg::BK;
+        splits = (p.K + kslice - 1) / kslice;
+        pgk_status ws;
+        float* P = (float*)workspace(WS_SPLITK, sizeof(float) * (size_t)splits * p.M * p.N, &ws);
+        if (!P) return cudaErrorMemoryAllocation;
+        k_rb_splitk<Cfg, INT><<<dim3((unsigned)tiles, (unsigned)splits), Cfg::NT, Cfg::SMEM, st>>>(
+            p, P, kslice);
+        const long long total = (long long)p.M * p.N;
+        const int blocks = (int)std::min<long long>((total + 255) / 256, 4LL * m.sm_count);
+        k_splitk_reduce<INT><<<blocks, 256, 0, st>>>(p, P, splits);
+        return cudaGetLastError();
+    }
     if (Cfg::SMEM > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute((const void*)k_rb<Cfg, INT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);

@@ -73,3 +73,11 @@ def test_beta_and_every_leaf(dev):
             torch.cuda.synchronize()
             assert np.array_equal(Ct.cpu().numpy(), ref)
     assert seen == {0, 1, 2}
+
+
+def test_split_k_int32(dev):
+    A, B = _ops(48, 80, 9000, 21)
+    ref = oracle.gemm_i32(A, B)
+    for p in _progs():
+        if p.sr > 1:
+            assert np.array_equal(_run(dev, A, B, p), ref), p.as_tuple()

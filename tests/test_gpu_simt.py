@@ -163,3 +163,15 @@ def test_full_size_sampled_rows(dev, M, N, K):
     torch.cuda.synchronize()
     Cs = C[torch.from_numpy(rows).to(dev)].cpu().numpy()
     assert_fp32_gemm(Cs, A, B, rows=rows)
+
+
+@pytest.mark.parametrize("M,N,K", [(64, 64, 8192), (100, 70, 5000), (256, 64, 16384)])
+def test_split_k_exact_on_integers(dev, M, N, K):
+    """Few output tiles and a long K take the split-K path (slices summed in
+    order); integer-valued FP32 operands keep every partial sum exact, so the
+    result must equal the oracle bit for bit, for every register-blocked variant."""
+    A, B = inputs.gemm_operands(M, N, K, seed=K, dist="integers")
+    ref = oracle.gemm(A, B)
+    for prog in _all_simt_params():
+        if prog.sr > 1:
+            assert np.array_equal(_run(dev, A, B, prog).astype(np.float64), ref), prog.as_tuple()
