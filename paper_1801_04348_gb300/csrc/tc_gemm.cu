@@ -459,8 +459,11 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 const int nchunks = (nkb + Cfg::CHUNK - 1) / Cfg::CHUNK;
                 // FP8: the scales of chunk ch + 1 are fetched while chunk ch is waited
                 // for and folded, keeping the global-load latency off that path
+                // a warp whose columns all lie beyond N stores nothing; its scale
+                // index is clamped so that the load stays inside the array
+                const int nblk = min(n0 / 128, nsb - 1);
                 auto chunk_scale = [&](int c) {
-                    return __ldg(p.sA + (size_t)tm * ksa + c) * __ldg(p.sB + (size_t)c * nsb + n0 / 128);
+                    return __ldg(p.sA + (size_t)tm * ksa + c) * __ldg(p.sB + (size_t)c * nsb + nblk);
                 };
                 float sc_next = Cfg::MODE == MODE_FP8 ? chunk_scale(0) : 1.f;
                 for (int ch = 0; ch < nchunks; ++ch) {
