@@ -14,6 +14,8 @@ grouped    512 FP32 GEMMs, M, N, K log-uniform in [32, 2048] (multiples of 16, s
 mm         the paper's Table "mm" grid on GB300: int32, n = 2^10 and 2^11, (ub1, B0) x s.
 transpose  the paper's transposition grid at order 2^14 (GB/s).
 jacobi     the paper's 1D Jacobi grid (T = 4, length 2^15 + 2; and 2^27 + 2).
+errmeas    the FP64 error reduction on 8192^2 (GB/s).
+mlp        the cost-model kernels (forward, minibatch gradient + Adam, full gradient).
 precision  8192^3, normal(0,1) and row-scaled by 10^uniform(-3,3): every form's step
            time (FP32 in/out, preparation included), kernel time on prepared operands,
            and relative Frobenius error on 64 sampled rows against the FP64 oracle.
@@ -295,6 +297,46 @@ def jacobi_table(dev, stream):
     return {"config": "1D Jacobi", "sizes": out}
 
 
+def errmeas(dev, stream):
+    """FP64 relative-error reduction over an 8192 x 8192 FP32 result against an FP64
+    reference: time and GB/s of its compulsory traffic (4 + 8 bytes per entry)."""
+    import torch
+    n = 8192
+    C = torch.randn(n, n, device=dev)
+    R = C.double() + 1e-3
+    out = torch.zeros(2, dtype=torch.float64, device=dev)
+    run = lambda: pgk.relerr(C, R, out, stream=stream.cuda_stream)
+    run()
+    ms = _events_ms(run, 20, stream)
+    return {"config": "relerr 8192^2", "ms": ms, "gbs": 12.0 * n * n / ms / 1e6}
+
+
+def mlp_kernels(dev, stream):
+    """Cost-model kernels: forward over 30 000 candidate rows, one minibatch
+    gradient (256 rows) + Adam step, and a 15 000-row full-batch gradient."""
+    import torch
+    rng = np.random.default_rng(0)
+    X = torch.from_numpy(rng.standard_normal((30000, 7)).astype(np.float32)).to(dev)
+    t = torch.from_numpy(rng.standard_normal(30000).astype(np.float32)).to(dev)
+    th = torch.from_numpy(inputs.he_uniform_mlp(0)).to(dev)
+    y = torch.empty(30000, device=dev)
+    g = torch.zeros_like(th)
+    m = torch.zeros_like(th)
+    v = torch.zeros_like(th)
+    loss = torch.zeros(1, device=dev)
+    sh = stream.cuda_stream
+    idx = torch.arange(256, dtype=torch.int32, device=dev)
+    fwd = lambda: pgk.mlp_forward(X, th, y, stream=sh)
+    step = lambda: (pgk.mlp_loss_grad(X, t, th, g, loss, idx=idx, stream=sh),
+                    pgk.mlp_adam(th, g, m, v, 1, stream=sh))
+    full = lambda: pgk.mlp_loss_grad(X[:15000], t[:15000], th, g, loss, stream=sh)
+    for f in (fwd, step, full):
+        f()
+    return {"config": "cost-model kernels", "forward_30000_ms": _events_ms(fwd, 20, stream),
+            "minibatch_step_ms": _events_ms(step, 20, stream),
+            "full_gradient_15000_ms": _events_ms(full, 20, stream)}
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
@@ -306,7 +348,8 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
     fns = {"config1": config1, "scale": scale, "grouped": grouped, "precision": precision,
-           "mm": mm_table, "transpose": transpose_table, "jacobi": jacobi_table}
+           "mm": mm_table, "transpose": transpose_table, "jacobi": jacobi_table,
+           "errmeas": errmeas, "mlp": mlp_kernels}
     for w in args.which:
         t0 = time.time()
         with torch.cuda.stream(stream):
