@@ -150,9 +150,12 @@ static int simt_candidates(int rb_family, pgk_params* out, int cap) {
 static int tc_candidates(pgk_dtype dtype, pgk_params* out, int cap) {
     std::vector<pgk_params> c;
     if (dtype == PGK_SPLIT_BF16) {
-        pgk_params a = {128, 128, 3, 0, 0}, b = {128, 256, 2, 0, 0};
+        pgk_params a = {128, 128, 3, 0, 0}, b = {128, 256, 2, 0, 0}, d = {128, 256, 4, 0, 0},
+                   e = {128, 128, 6, 0, 0};
         c.push_back(a);
         c.push_back(b);
+        c.push_back(d);
+        c.push_back(e);
     } else if (dtype == PGK_BF16) {
         pgk_params a = {128, 256, 4, 0, 0}, b = {128, 128, 6, 0, 0}, d = {128, 256, 3, 0, 0},
                    e = {128, 128, 4, 0, 0};

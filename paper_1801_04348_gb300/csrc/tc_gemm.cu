@@ -31,7 +31,10 @@
 
 namespace pgk {
 
-enum { MODE_BF16 = 0, MODE_SPLIT = 1, MODE_FP8 = 2 };
+// MODE_SPLIT stages hi and lo of both operands together and issues the three
+// products per K step; MODE_SPLIT3 runs three BF16-sized passes per K block
+// ((lo_a, hi_b), (hi_a, lo_b), (hi_a, hi_b)) for a deeper pipeline.
+enum { MODE_BF16 = 0, MODE_SPLIT = 1, MODE_FP8 = 2, MODE_SPLIT3 = 3 };
 
 static constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ULL;  // 4 s
 static constexpr unsigned int ERR_TIMEOUT_PRODUCER = 0x1u;
@@ -49,13 +52,15 @@ struct TcCfg {
     static constexpr int NKSUB = BK / UK;                   // MMAs per stage and product
     static constexpr int A_BYTES = BM * 128;
     static constexpr int B_BYTES = BN * 128;
-    static constexpr int NOPS = MODE == MODE_SPLIT ? 2 : 1; // hi/lo pairs
+    static constexpr int NOPS = MODE == MODE_SPLIT ? 2 : 1; // hi/lo pairs per stage
+    static constexpr int PASSES = MODE == MODE_SPLIT3 ? 3 : 1;  // stages per K block
     static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
     // K blocks accumulated in tensor memory before the epilogue folds the chunk
     // into FP32 registers (0 = whole K in tensor memory).  FP8: every 128-deep
     // chunk carries its own scales.  Split: 512-deep chunks bound the growth
     // of the tensor-core accumulator, the dominant error at large K.
-    static constexpr int CHUNK = MODE == MODE_FP8 ? 1 : (MODE == MODE_SPLIT ? 8 : 0);
+    static constexpr int CHUNK =
+        MODE == MODE_FP8 ? 1 : ((MODE == MODE_SPLIT || MODE == MODE_SPLIT3) ? 8 : 0);
     static constexpr int EPI_WARPS = CHUNK == 0 ? 4 : 8;
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
     // tensor-memory accumulators in flight: FP8 with 128-wide tiles keeps four
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         tmap_prefetch(&tmA);
         tmap_prefetch(&tmB);
-        if (Cfg::MODE == MODE_SPLIT) {
+        if (Cfg::MODE == MODE_SPLIT || Cfg::MODE == MODE_SPLIT3) {
             tmap_prefetch(&tmA2);
             tmap_prefetch(&tmB2);
         }
@@ -300,7 +305,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 int tm, tn;
                 coords(t, tm, tn);
-                for (int kb = 0; kb < nkb; ++kb) {
+                for (int kb = 0; kb < nkb && ok; ++kb)
+                for (int v = 0; v < Cfg::PASSES; ++v) {
                     if (!mbar_wait(&empty_bar[stage], phase ^ 1u, abort_flag, p.err,
                                    ERR_TIMEOUT_PRODUCER)) {
                         ok = false;
@@ -309,8 +315,11 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     uint8_t* st = tiles + (size_t)stage * Cfg::STAGE_BYTES;
                     mbar_arrive_expect_tx(&full_bar[stage], Cfg::STAGE_BYTES);
                     const int x = kb * Cfg::BK;
-                    tma_load_2d(st, &tmA, &full_bar[stage], x, tm * Cfg::BM);
-                    tma_load_2d(st + Cfg::A_BYTES, &tmB, &full_bar[stage], x, tn * Cfg::BN);
+                    // passes of MODE_SPLIT3: 0 = (A lo, B hi), 1 = (A hi, B lo), 2 = (A hi, B hi)
+                    const CUtensorMap* ma = (Cfg::MODE == MODE_SPLIT3 && v == 0) ? &tmA2 : &tmA;
+                    const CUtensorMap* mb = (Cfg::MODE == MODE_SPLIT3 && v == 1) ? &tmB2 : &tmB;
+                    tma_load_2d(st, ma, &full_bar[stage], x, tm * Cfg::BM);
+                    tma_load_2d(st + Cfg::A_BYTES, mb, &full_bar[stage], x, tn * Cfg::BN);
                     if (Cfg::MODE == MODE_SPLIT) {
                         tma_load_2d(st + Cfg::A_BYTES + Cfg::B_BYTES, &tmA2, &full_bar[stage], x,
                                     tm * Cfg::BM);
@@ -369,41 +378,44 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                         }
                         tc_fence_after();
                     }
-                    if (!mbar_wait(&full_bar[stage], phase, abort_flag, p.err, ERR_TIMEOUT_MMA)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t d = tmem_base + (uint32_t)(acc * Cfg::BN);
-                    const uint32_t sa = smem_u32(tiles + (size_t)stage * Cfg::STAGE_BYTES);
-                    const uint32_t sb = sa + Cfg::A_BYTES;
+                    for (int v = 0; v < Cfg::PASSES; ++v) {
+                        if (!mbar_wait(&full_bar[stage], phase, abort_flag, p.err, ERR_TIMEOUT_MMA)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d = tmem_base + (uint32_t)(acc * Cfg::BN);
+                        const uint32_t sa = smem_u32(tiles + (size_t)stage * Cfg::STAGE_BYTES);
+                        const uint32_t sb = sa + Cfg::A_BYTES;
 #pragma unroll
-                    for (int ks = 0; ks < Cfg::NKSUB; ++ks) {
-                        const uint32_t koff = (uint32_t)ks * 32u;  // 32 bytes of K per MMA
-                        const uint64_t da = sdesc_k128(sa + koff);
-                        const uint64_t db = sdesc_k128(sb + koff);
-                        const uint32_t accum = (kin > 0 || ks > 0) ? 1u : 0u;
-                        if (Cfg::MODE == MODE_FP8) {
-                            mma_f8(d, da, db, idesc, accum);
-                        } else if (Cfg::MODE == MODE_BF16) {
-                            mma_f16(d, da, db, idesc, accum);
-                        } else {
-                            const uint32_t sa2 = sb + Cfg::B_BYTES;   // A lo
-                            const uint32_t sb2 = sa2 + Cfg::A_BYTES;  // B lo
-                            const uint64_t da2 = sdesc_k128(sa2 + koff);
-                            const uint64_t db2 = sdesc_k128(sb2 + koff);
-                            // small terms first: lo*hi, hi*lo, then hi*hi
-                            mma_f16(d, da2, db, idesc, accum);
-                            mma_f16(d, da, db2, idesc, 1u);
-                            mma_f16(d, da, db, idesc, 1u);
+                        for (int ks = 0; ks < Cfg::NKSUB; ++ks) {
+                            const uint32_t koff = (uint32_t)ks * 32u;  // 32 bytes of K per MMA
+                            const uint64_t da = sdesc_k128(sa + koff);
+                            const uint64_t db = sdesc_k128(sb + koff);
+                            const uint32_t accum = (kin > 0 || v > 0 || ks > 0) ? 1u : 0u;
+                            if (Cfg::MODE == MODE_FP8) {
+                                mma_f8(d, da, db, idesc, accum);
+                            } else if (Cfg::MODE == MODE_BF16 || Cfg::MODE == MODE_SPLIT3) {
+                                mma_f16(d, da, db, idesc, accum);
+                            } else {
+                                const uint32_t sa2 = sb + Cfg::B_BYTES;   // A lo
+                                const uint32_t sb2 = sa2 + Cfg::A_BYTES;  // B lo
+                                const uint64_t da2 = sdesc_k128(sa2 + koff);
+                                const uint64_t db2 = sdesc_k128(sb2 + koff);
+                                // small terms first: lo*hi, hi*lo, then hi*hi
+                                mma_f16(d, da2, db, idesc, accum);
+                                mma_f16(d, da, db2, idesc, 1u);
+                                mma_f16(d, da, db, idesc, 1u);
+                            }
+                        }
+                        issued_any = true;
+                        mma_commit(&empty_bar[stage]);
+                        if (++stage == Cfg::STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
                         }
                     }
-                    issued_any = true;
-                    mma_commit(&empty_bar[stage]);
-                    if (++stage == Cfg::STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
+                    if (!ok) break;
                     if (Cfg::CHUNK > 0 && (kin == Cfg::CHUNK - 1 || kb == nkb - 1)) {
                         mma_commit(&accf_bar[acc]);
                         if (++acc == Cfg::ACC_BUFS) {
@@ -681,6 +693,7 @@ static const TcVariant* tc_table(int* n) {
         tcv<MODE_BF16, 256, 4>(PGK_FAM_TC_BF16),   tcv<MODE_BF16, 128, 6>(PGK_FAM_TC_BF16),
         tcv<MODE_BF16, 256, 3>(PGK_FAM_TC_BF16),   tcv<MODE_BF16, 128, 4>(PGK_FAM_TC_BF16),
         tcv<MODE_SPLIT, 128, 3>(PGK_FAM_TC_SPLIT), tcv<MODE_SPLIT, 256, 2>(PGK_FAM_TC_SPLIT),
+        tcv<MODE_SPLIT3, 256, 4>(PGK_FAM_TC_SPLIT), tcv<MODE_SPLIT3, 128, 6>(PGK_FAM_TC_SPLIT),
         tcv<MODE_FP8, 128, 6>(PGK_FAM_TC_FP8),     tcv<MODE_FP8, 256, 4>(PGK_FAM_TC_FP8),
     };
     *n = (int)(sizeof(t) / sizeof(t[0]));

@@ -11,7 +11,7 @@ from paper_1801_04348_gb300 import inputs, pgk
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = {pgk.BF16: [(256, 4), (128, 6), (256, 3), (128, 4)], pgk.SPLIT_BF16: [(128, 3), (256, 2)],
+VARIANTS = {pgk.BF16: [(256, 4), (128, 6), (256, 3), (128, 4)], pgk.SPLIT_BF16: [(128, 3), (256, 2), (256, 4), (128, 6)],
             pgk.FP8_E4M3: [(128, 6), (256, 4)]}
 
 
