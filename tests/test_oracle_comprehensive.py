@@ -1,9 +1,41 @@
 """Pins for the Algorithms 1-2 oracle: it must reproduce the case systems the
 paper prints for its own examples (Fig. "compparkern", Section 1; Fig. "1dj" and
 Fig. "transpose", Section 5) and satisfy Definition 2 (coverage, partition)."""
+import json
+import os
+import re
+
 import numpy as np
 
 from oracle import comprehensive as co
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "printed_case_systems.json")))
+
+
+def _printed(example, program, box):
+    """Union over the printed systems of `program`, evaluated on the box.  Each
+    inequality is a chain a op b [op c] with op in {<=, <}; terms are products
+    and sums of symbols and integers."""
+    def term(t):
+        val = 0
+        for summand in t.split("+"):
+            prod = 1
+            for f in summand.split("*"):
+                f = f.strip()
+                prod = prod * (int(f) if f.isdigit() else box[f])
+            val = val + prod
+        return val
+
+    out = np.zeros(len(next(iter(box.values()))), dtype=bool)
+    for system in GOLDEN[example]["cases"][program]:
+        ok = np.ones_like(out)
+        for ineq in system:
+            parts = re.split(r"(<=|<)", ineq)
+            for i in range(0, len(parts) - 2, 2):
+                a, op, b = term(parts[i]), parts[i + 1], term(parts[i + 2])
+                ok &= (a <= b) if op == "<=" else (a < b)
+        out |= ok
+    return out
 
 
 def _region(leaves, prog_pred, box):
@@ -33,9 +65,8 @@ def test_matrix_add_example_reproduces_C1_C2():
     assert sorted(p["kernel"] for p, _, _ in leaves) == ["K1", "K2"]
     k1 = _region(leaves, lambda p: p["kernel"] == "K1", box)
     k2 = _region(leaves, lambda p: p["kernel"] == "K2", box)
-    fits = box["B0"] * box["B1"] <= box["T"]
-    assert np.array_equal(k1, fits & (14 <= box["R"]))                      # C1
-    assert np.array_equal(k2, fits & (10 <= box["R"]) & (box["R"] < 14))    # C2
+    assert np.array_equal(k1, _printed("matrix_add", "K1", box))            # C1
+    assert np.array_equal(k2, _printed("matrix_add", "K2", box))            # C2
     assert not np.any(k1 & k2)
 
 
@@ -54,7 +85,7 @@ def _three_case_tree(smem_s, smem_1, regs_full, regs_reduced, reg_sigma):
 
     strategies = {"3b": co.Strategy("3b", False, gran), "4b": co.Strategy("4b", False, nocache)}
     box = co.make_box({"ZB": range(0, 300, 2), "RB": range(0, 14), "s": [2, 4, 8], "B": [4, 8, 16],
-                       "B0": [1], "B1": [1]})
+                       "B0": [2, 4, 8], "B1": [2, 4, 8]})
     Q = co.initial_quintuple({"case": "4a3a", "smem": smem_s, "regs": regs_full},
                              ["3b", "4b"], ["regs", "smem"], [])
     return co.comprehensive_optimization(Q, counters, strategies, box), box
@@ -63,13 +94,9 @@ def _three_case_tree(smem_s, smem_1, regs_full, regs_reduced, reg_sigma):
 def test_jacobi_example_three_cases():
     # Fig. "1dj": 2sB+2 <= Z_B ; 2B+2 <= Z_B < 2sB+2 ; Z_B < 2B+2 ; all with 9 <= R_B
     leaves, box = _three_case_tree(lambda e: 2 * e["s"] * e["B"] + 2, lambda e: 2 * e["B"] + 2, 9, 9, ())
-    ZB, RB, s, B = box["ZB"], box["RB"], box["s"], box["B"]
-    r1 = _region(leaves, lambda p: p["case"] == "4a3a", box)
-    r2 = _region(leaves, lambda p: p["case"] == "3b4a", box)
-    r3 = _region(leaves, lambda p: p["case"] == "3b4b", box)
-    assert np.array_equal(r1, (2 * s * B + 2 <= ZB) & (9 <= RB))
-    assert np.array_equal(r2, (2 * B + 2 <= ZB) & (ZB < 2 * s * B + 2) & (9 <= RB))
-    assert np.array_equal(r3, (ZB < 2 * B + 2) & (9 <= RB))
+    for case in ("4a3a", "3b4a", "3b4b"):
+        got = _region(leaves, lambda p, c=case: p["case"] == c, box)
+        assert np.array_equal(got, _printed("jacobi", case, box)), case
 
 
 def test_transpose_example_printed_systems_are_sound():
@@ -77,20 +104,15 @@ def test_transpose_example_printed_systems_are_sound():
     # granularity also serves the register counter.  Every printed system must lie
     # inside the region the algorithm assigns to that program, and the three
     # regions must be disjoint.
-    leaves, box = _three_case_tree(lambda e: 2 * e["s"] * e["B"] * e["B"] + 0 * e["B0"],
-                                   lambda e: 2 * e["B"] * e["B"], 6, 5, ("3b",))
-    ZB, RB, s, B = box["ZB"], box["RB"], box["s"], box["B"]
+    leaves, box = _three_case_tree(lambda e: 2 * e["s"] * e["B0"] * e["B1"],
+                                   lambda e: 2 * e["B0"] * e["B1"], 6, 5, ("3b",))
+    RB = box["RB"]
     r1 = _region(leaves, lambda p: p["case"] == "4a3a", box)
     r2 = _region(leaves, lambda p: p["case"] == "3b4a", box)
     r3 = _region(leaves, lambda p: p["case"] == "3b4b", box)
-    P1 = (2 * s * B * B <= ZB) & (6 <= RB)
-    P2a = (2 * B * B <= ZB) & (ZB < 2 * s * B * B) & (5 <= RB)
-    P2b = P2a & (RB < 6)
-    P3a = (ZB < 2 * B * B) & (5 <= RB)
-    P3b = P3a & (RB < 6)
-    assert np.array_equal(r1, P1)
-    assert not np.any(P2a & ~r2) and not np.any(P2b & ~r2)
-    assert not np.any(P3a & ~r3) and not np.any(P3b & ~r3)
+    assert np.array_equal(r1, _printed("transpose", "4a3a", box))
+    assert not np.any(_printed("transpose", "3b4a", box) & ~r2)
+    assert not np.any(_printed("transpose", "3b4b", box) & ~r3)
     assert not np.any(r1 & r2) and not np.any(r1 & r3) and not np.any(r2 & r3)
     # coverage (Definition 2 (iii)): every point with at least 5 registers has a case
     assert np.array_equal(r1 | r2 | r3, RB >= 5)
