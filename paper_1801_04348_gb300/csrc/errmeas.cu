@@ -36,20 +36,23 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
     }
 }
 
+// Block b takes rows b, b + gridDim.x, ...; its threads stride over the columns
+// of a row (coalesced, no per-element division).
 __global__ void __launch_bounds__(256) k_relerr_partial(int rows, int cols, const float* __restrict__ C,
                                                        int ldc, const double* __restrict__ R, int ldr,
                                                        const int64_t* __restrict__ row_index,
                                                        double* __restrict__ partial) {
     double num = 0.0, den = 0.0;
-    const long long total = (long long)rows * cols;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(i / cols), c = (int)(i - (long long)r * cols);
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
         const long long cr = row_index ? row_index[r] : r;
-        const double ref = R[(size_t)r * ldr + c];
-        const double d = (double)C[(size_t)cr * ldc + c] - ref;
-        num = fma(d, d, num);
-        den = fma(ref, ref, den);
+        const float* crow = C + (size_t)cr * ldc;
+        const double* rrow = R + (size_t)r * ldr;
+        for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+            const double ref = __ldg(rrow + c);
+            const double d = (double)__ldg(crow + c) - ref;
+            num = fma(d, d, num);
+            den = fma(ref, ref, den);
+        }
     }
     block_sum2(num, den);
     if (threadIdx.x == 0) {
@@ -75,9 +78,7 @@ __global__ void __launch_bounds__(256) k_relerr_final(int nparts, const double* 
 pgk_status relerr_launch(int rows, int cols, const float* C, int ldc, const double* Cref, int ldr,
                          const int64_t* row_index, double* out, double* partial, int max_parts,
                          cudaStream_t st) {
-    const long long total = (long long)rows * cols;
-    int parts = (int)std::min<long long>((total + RELERR_THREADS - 1) / RELERR_THREADS, max_parts);
-    if (parts < 1) parts = 1;
+    const int parts = std::max(1, std::min(rows, max_parts));
     k_relerr_partial<<<parts, RELERR_THREADS, 0, st>>>(rows, cols, C, ldc, Cref, ldr, row_index,
                                                        partial);
     k_relerr_final<<<1, RELERR_THREADS, 0, st>>>(parts, partial, out);
