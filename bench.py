@@ -422,10 +422,11 @@ KERNEL_SOURCES = {"f32": ["simt_rb.cuh", "simt_f32.cu"], "split": ["tc_gemm.cu"]
 
 def recorded_traffic(form, prog):
     """DRAM bytes per GEMM launch from the committed ncu summary
-    profiles/traffic_<form>.txt, or None when that summary is missing, was taken
-    for other program parameters, or the kernel source changed since."""
+    profiles/traffic_<form>_<B0>-<B1>-<s>-<sr>-<tile>.txt, or None when that
+    summary is missing or the kernel source changed since it was taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"traffic_{form}.txt")
+    tag = "-".join(str(x) for x in prog.as_tuple())
+    path = os.path.join(ROOT, "profiles", f"traffic_{form}_{tag}.txt")
     if not os.path.exists(path):
         return None
     rec = {}
