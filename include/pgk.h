@@ -426,6 +426,20 @@ PGK_API pgk_status pgk_tune_cache_get(int M, int N, int K, pgk_dtype dtype, pgk_
 PGK_API pgk_status pgk_tune_cache_save(const char* path);
 PGK_API pgk_status pgk_tune_cache_load(const char* path);
 
+/* ------------------------------------------------------------ measurement */
+
+/* FP32 SIMT throughput probe, a measurement utility with no counterpart in the
+ * paper: the measured FP32 peak that the GEMM kernels' SIMT fraction can be
+ * compared with, beside the derived SM count x 128 lanes x 2 flop x clock.
+ * Launches `blocks` blocks of 256 threads; each thread runs `iters` iterations
+ * of 16 independent FMA chains, paired (fma.rn.f32x2, 2 FMAs per chain step)
+ * when `paired` is nonzero, else scalar.  Flops per launch:
+ * blocks x 256 x iters x 16 x (paired ? 2 : 1) x 2.  `sink` is a device float
+ * array of blocks x 256 entries that receives one value per thread (written
+ * only so that the work is kept).  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, CUDA. */
+PGK_API pgk_status pgk_simt_peak_probe(int blocks, int iters, int paired, float* sink, void* stream);
+
 /* ------------------------------------------------------------- status */
 
 /* Reads and clears the device error word that bounded waits set (synchronises

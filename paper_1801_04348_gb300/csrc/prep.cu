@@ -130,54 +130,104 @@ __global__ void __launch_bounds__(256) k_cvt_transpose(int rows, int cols,
     }
 }
 
-// Per-tile FP8 quantisation: one block per 128 x 128 tile of src.
-__global__ void __launch_bounds__(256) k_quant_fp8(int rows, int cols, const float* __restrict__ src,
-                                                   int lds, uint8_t* __restrict__ dst, int ldd,
-                                                   float* __restrict__ scales, int ld_scales,
-                                                   int transpose) {
-    __shared__ float red[8];
-    __shared__ uint8_t tile[128][132];
-    const int ti = blockIdx.y, tj = blockIdx.x;
-    const int r0 = ti * 128, c0 = tj * 128;
-    const int tid = threadIdx.x;
-    // pass 1: amax (|x| is exact, max is order independent)
-    float amax = 0.f;
-    for (int idx = tid; idx < 128 * 128; idx += 256) {
-        const int r = r0 + idx / 128, c = c0 + idx % 128;
-        if (r < rows && c < cols) amax = fmaxf(amax, fabsf(__ldg(src + (size_t)r * lds + c)));
+// Four consecutive elements of row r starting at column c (c a multiple of 4),
+// zero outside the matrix; one 128-bit load when the row allows it.
+__device__ __forceinline__ float4 load_row4(const float* __restrict__ src, int lds, int rows,
+                                            int cols, int r, int c, int vec) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r >= rows || c >= cols) return v;
+    const float* p = src + (size_t)r * lds + c;
+    if (vec && c + 3 < cols) return __ldg(reinterpret_cast<const float4*>(p));
+    v.x = __ldg(p);
+    if (c + 1 < cols) v.y = __ldg(p + 1);
+    if (c + 2 < cols) v.z = __ldg(p + 2);
+    if (c + 3 < cols) v.w = __ldg(p + 3);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t e4m3(float x, float scale) {
+    // binary32 division rounded to nearest, then E4M3 round to nearest even, saturated
+    return (uint32_t)__nv_cvt_float_to_fp8(__fdiv_rn(x, scale), __NV_SATFINITE, __NV_E4M3);
+}
+
+// Writes the four codes of word w (byte k = element k) to dst + off, or the
+// in-range ones among them (n of 4) one by one.
+__device__ __forceinline__ void store_codes(uint8_t* __restrict__ dst, size_t off, uint32_t w,
+                                            int n, int vec) {
+    if (n <= 0) return;
+    if (vec && n == 4) {
+        *reinterpret_cast<uint32_t*>(dst + off) = w;
+        return;
     }
+    for (int k = 0; k < n; ++k) dst[off + k] = (uint8_t)(w >> (8 * k));
+}
+
+// Per-tile FP8 quantisation: one block of QUANT_THREADS per 128 x 128 tile.  The
+// tile is read from global memory once, into registers: warp w, lane l holds rows
+// 16 i + w, columns 4 l .. 4 l + 3 (each warp load is one 512-byte row segment).
+// The block's amax gives the scale.  Row output: each warp writes 128 contiguous
+// bytes of a row.  Transposed output: the codes go through a shared tile with a
+// row pitch of 129 bytes (conflict-free both for the row-wise stores and for the
+// column-wise reads), and each warp writes whole 128-byte rows of the transpose.
+static constexpr int QUANT_THREADS = 512;
+static constexpr int QUANT_PITCH = 129;
+
+template <bool TRANS>
+__global__ void __launch_bounds__(QUANT_THREADS) k_quant_fp8(int rows, int cols,
+                                                             const float* __restrict__ src, int lds,
+                                                             uint8_t* __restrict__ dst, int ldd,
+                                                             float* __restrict__ scales, int ld_scales,
+                                                             int vec_in, int vec_out) {
+    constexpr int WARPS = QUANT_THREADS / 32;          // 16
+    constexpr int NV = 128 * 128 / 4 / QUANT_THREADS;  // float4 per thread: 8
+    __shared__ float red[WARPS];
+    __shared__ uint8_t tile[TRANS ? 128 * QUANT_PITCH : 1];
+    const int r0 = blockIdx.y * 128, c0 = blockIdx.x * 128;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = load_row4(src, lds, rows, cols, r0 + i * WARPS + warp, c0 + lane * 4, vec_in);
+    // amax (|x| is exact and max is order independent; out-of-range elements are 0)
+    float amax = 0.f;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[i].x), fabsf(v[i].y)),
+                                 fmaxf(fabsf(v[i].z), fabsf(v[i].w))));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if ((tid & 31) == 0) red[tid >> 5] = amax;
-    __syncthreads();
-    if (tid < 32) {
-        float a = tid < 8 ? red[tid] : 0.f;
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
-        if (tid == 0) red[0] = a;
-    }
+    if (lane == 0) red[warp] = amax;
     __syncthreads();
     amax = red[0];
-    const float scale = amax == 0.f ? 1.f : amax / 448.f;   // IEEE division
-    if (tid == 0) scales[(size_t)ti * ld_scales + tj] = scale;
-    // pass 2: quantise (IEEE division, round to nearest even, saturate to +-448)
-    for (int idx = tid; idx < 128 * 128; idx += 256) {
-        const int rr = idx / 128, cc = idx % 128;
-        const int r = r0 + rr, c = c0 + cc;
-        uint8_t q = 0;
-        if (r < rows && c < cols) {
-            const float x = __ldg(src + (size_t)r * lds + c);
-            q = (uint8_t)__nv_cvt_float_to_fp8(x / scale, __NV_SATFINITE, __NV_E4M3);
-            if (!transpose) dst[(size_t)r * ldd + c] = q;
+#pragma unroll
+    for (int w = 1; w < WARPS; ++w) amax = fmaxf(amax, red[w]);
+    const float scale = amax == 0.f ? 1.f : __fdiv_rn(amax, 448.f);
+    if (threadIdx.x == 0) scales[(size_t)blockIdx.y * ld_scales + blockIdx.x] = scale;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int rr = i * WARPS + warp, cc = lane * 4;   // position in the tile
+        const uint32_t w = e4m3(v[i].x, scale) | (e4m3(v[i].y, scale) << 8) |
+                           (e4m3(v[i].z, scale) << 16) | (e4m3(v[i].w, scale) << 24);
+        if (TRANS) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tile[rr * QUANT_PITCH + cc + k] = (uint8_t)(w >> (8 * k));
+        } else if (r0 + rr < rows) {
+            store_codes(dst, (size_t)(r0 + rr) * ldd + c0 + cc, w, min(4, cols - c0 - cc), vec_out);
         }
-        tile[rr][cc] = q;
     }
-    if (transpose) {
+    if (TRANS) {
         __syncthreads();
-        for (int idx = tid; idx < 128 * 128; idx += 256) {
-            const int cc = idx / 128, rr = idx % 128;   // dst row c0+cc, dst col r0+rr
-            const int r = r0 + rr, c = c0 + cc;
-            if (r < rows && c < cols) dst[(size_t)c * ldd + r] = tile[rr][cc];
+        // output row j of the tile = source column c0 + j; lane l writes source rows
+        // r0 + 4 l .. r0 + 4 l + 3 of it
+#pragma unroll
+        for (int jj = 0; jj < 128 / WARPS; ++jj) {
+            const int j = warp * (128 / WARPS) + jj;
+            if (c0 + j >= cols) break;
+            const uint8_t* col = tile + (4 * lane) * QUANT_PITCH + j;
+            const uint32_t w = (uint32_t)col[0] | ((uint32_t)col[QUANT_PITCH] << 8) |
+                               ((uint32_t)col[2 * QUANT_PITCH] << 16) |
+                               ((uint32_t)col[3 * QUANT_PITCH] << 24);
+            store_codes(dst, (size_t)(c0 + j) * ldd + r0 + 4 * lane, w, min(4, rows - r0 - 4 * lane),
+                        vec_out);
         }
     }
 }
@@ -224,7 +274,14 @@ pgk_status launch_quant_fp8(int rows, int cols, const float* src, int lds, uint8
         set_error("too many rows for FP8 quantisation");
         return PGK_ERR_INVALID_ARG;
     }
-    k_quant_fp8<<<grid, 256, 0, st>>>(rows, cols, src, lds, dst, ldd, scales, ld_scales, transpose);
+    const int vec_in = aligned(src, 16) && lds % 4 == 0;
+    const int vec_out = aligned(dst, 4) && ldd % 4 == 0;
+    if (transpose)
+        k_quant_fp8<true><<<grid, QUANT_THREADS, 0, st>>>(rows, cols, src, lds, dst, ldd, scales,
+                                                          ld_scales, vec_in, vec_out);
+    else
+        k_quant_fp8<false><<<grid, QUANT_THREADS, 0, st>>>(rows, cols, src, lds, dst, ldd, scales,
+                                                           ld_scales, vec_in, vec_out);
     PGK_CUDA_TRY(cudaGetLastError(), "FP8 quantisation launch");
     return PGK_OK;
 }

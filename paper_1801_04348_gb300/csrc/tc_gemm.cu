@@ -213,6 +213,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr));
 }
 
+// Paired FP32 arithmetic for the chunk fold: two IEEE fused multiply-adds
+// (the rounding of fmaf) per instruction on a 64-bit register pair.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_fma(uint64_t& acc, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ float f2_lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+
 __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -258,7 +271,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         }
         for (int b = 0; b < Cfg::ACC_BUFS; ++b) {
             mbar_init(&accf_bar[b], 1);
-            mbar_init(&acce_bar[b], Cfg::EPI_WARPS * 32);
+            mbar_init(&acce_bar[b], Cfg::EPI_WARPS);   // one arrival per epilogue warp
         }
         mbar_init(&drain_bar, 1);
         abort_sh = 0;
@@ -464,23 +477,31 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             const bool row_ok = row < p.M;
             const bool vec = ((p.ldc & 3) == 0) && ((((uintptr_t)p.C) & 15u) == 0);
             if (Cfg::CHUNK > 0) {
-                float accr[Cfg::BN / (Cfg::EPI_WARPS / 4)];
+                constexpr int NCOL = Cfg::BN / (Cfg::EPI_WARPS / 4);
+                // running FP32 sums as pairs: acc2[j] holds columns 2j, 2j + 1
+                uint64_t acc2[NCOL / 2];
 #pragma unroll
-                for (int j = 0; j < ncol; ++j) accr[j] = 0.f;
+                for (int j = 0; j < NCOL / 2; ++j) acc2[j] = 0ull;
                 const int ksa = (p.K + 127) / 128, nsb = (p.N + 127) / 128;
                 const int nchunks = (nkb + Cfg::CHUNK - 1) / Cfg::CHUNK;
-                // FP8: the scales of chunk ch + 1 are fetched while chunk ch is waited
-                // for and folded, keeping the global-load latency off that path
-                // a warp whose columns all lie beyond N stores nothing; its scale
-                // index is clamped so that the load stays inside the array
+                // FP8 chunk factors sA * sB, 32 chunks per window: lane j holds the factor
+                // of chunk 32 w + j of the current window (cur) and of the next one (nxt),
+                // loaded a whole window before use, so that the global-load latency never
+                // sits on the fold; each chunk takes its factor by a warp shuffle.  A warp
+                // whose columns all lie beyond N stores nothing; its scale index is
+                // clamped so that the loads stay inside the array.
                 const int nblk = min(n0 / 128, nsb - 1);
                 auto chunk_scale = [&](int c) {
-                    return __ldg(p.sA + (size_t)tm * ksa + c) * __ldg(p.sB + (size_t)c * nsb + nblk);
+                    return c < nchunks
+                        ? __ldg(p.sA + (size_t)tm * ksa + c) * __ldg(p.sB + (size_t)c * nsb + nblk)
+                        : 0.f;
                 };
-                float sc_next = Cfg::MODE == MODE_FP8 ? chunk_scale(0) : 1.f;
+                float sc_cur = 1.f, sc_nxt = 1.f;
+                if (Cfg::MODE == MODE_FP8) {
+                    sc_cur = chunk_scale(lane);
+                    sc_nxt = chunk_scale(32 + lane);
+                }
                 for (int ch = 0; ch < nchunks; ++ch) {
-                    const float sc = sc_next;
-                    if (Cfg::MODE == MODE_FP8 && ch + 1 < nchunks) sc_next = chunk_scale(ch + 1);
                     int w = 1;
                     if (lane == 0)
                         w = mbar_wait(&accf_bar[acc], acc_phase, abort_flag, p.err,
@@ -493,12 +514,19 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     while (!mbar_try_wait(&accf_bar[acc], acc_phase)) {
                     }
                     tc_fence_after();
-                    // chunk sum times sA * sB (FP8: the tile scales of this 128-deep chunk)
-                    // loads issued per wait: both of a 64-column slice, else 32 columns
-                    // at a time (128-column slices keep 128 accumulators in registers)
-                    constexpr int NB = Cfg::BN / (Cfg::EPI_WARPS / 4) == 64 ? 2 : 1;
+                    const float sc = Cfg::MODE == MODE_FP8 ? __shfl_sync(0xffffffffu, sc_cur, ch & 31) : 1.f;
+                    if (Cfg::MODE == MODE_FP8 && (ch & 31) == 31) {
+                        sc_cur = sc_nxt;
+                        sc_nxt = chunk_scale(ch + 33 + lane);
+                    }
+                    // sum += chunk * sc with one rounding per element: FP8 sc = sA * sB (the
+                    // tile scales of this 128-deep chunk); split sc = 1, i.e. sum + chunk.
+                    // Two 32-column loads are in flight per wait, except for the split
+                    // form's 128-column slices (a fold every 8 K blocks, off the critical path)
+                    const uint64_t sc2 = f2_pack(sc, sc);
+                    constexpr int NB = (NCOL == 64 || Cfg::MODE == MODE_FP8) ? 2 : 1;
 #pragma unroll
-                    for (int c0 = 0; c0 < ncol / 32; c0 += NB) {
+                    for (int c0 = 0; c0 < NCOL / 32; c0 += NB) {
                         uint32_t r[NB][32];
 #pragma unroll
                         for (int c = 0; c < NB; ++c)
@@ -509,14 +537,14 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
 #pragma unroll
                         for (int c = 0; c < NB; ++c)
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                float& a = accr[(c0 + c) * 32 + j];
-                                if (Cfg::MODE == MODE_FP8) a = fmaf(__uint_as_float(r[c][j]), sc, a);
-                                else a += __uint_as_float(r[c][j]);
-                            }
+                            for (int j = 0; j < 16; ++j)
+                                f2_fma(acc2[(c0 + c) * 16 + j],
+                                       f2_pack(__uint_as_float(r[c][2 * j]), __uint_as_float(r[c][2 * j + 1])),
+                                       sc2);
                     }
                     tc_fence_before();
-                    mbar_arrive(&acce_bar[acc]);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acce_bar[acc]);
                     if (++acc == Cfg::ACC_BUFS) {
                         acc = 0;
                         acc_phase ^= 1u;
@@ -525,10 +553,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 if (!ok) break;
                 if (row_ok) {
 #pragma unroll
-                    for (int j = 0; j < ncol; j += 4) {
+                    for (int j = 0; j < NCOL; j += 4) {
                         const int n = n0 + j;
+                        const float v4[4] = {f2_lo(acc2[j / 2]), f2_hi(acc2[j / 2]),
+                                             f2_lo(acc2[j / 2 + 1]), f2_hi(acc2[j / 2 + 1])};
                         if (vec && n + 3 < p.N) {
-                            float4 o = make_float4(accr[j], accr[j + 1], accr[j + 2], accr[j + 3]);
+                            float4 o = make_float4(v4[0], v4[1], v4[2], v4[3]);
                             if (p.beta) {
                                 const float4 c = *reinterpret_cast<const float4*>(crow + n);
                                 o.x += c.x; o.y += c.y; o.z += c.z; o.w += c.w;
@@ -536,8 +566,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                             *reinterpret_cast<float4*>(crow + n) = o;
                         } else {
                             for (int u = 0; u < 4; ++u)
-                                if (n + u < p.N)
-                                    crow[n + u] = p.beta ? crow[n + u] + accr[j + u] : accr[j + u];
+                                if (n + u < p.N) crow[n + u] = p.beta ? crow[n + u] + v4[u] : v4[u];
                         }
                     }
                 }
@@ -585,7 +614,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(&acce_bar[acc]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce_bar[acc]);
                 if (++acc == Cfg::ACC_BUFS) {
                     acc = 0;
                     acc_phase ^= 1u;

@@ -16,6 +16,10 @@ transpose  the paper's transposition grid at order 2^14 (GB/s).
 jacobi     the paper's 1D Jacobi grid (T = 4, length 2^15 + 2; and 2^27 + 2).
 errmeas    the FP64 error reduction on 8192^2 (GB/s).
 mlp        the cost-model kernels (forward, minibatch gradient + Adam, full gradient).
+forms      every form (FP32, BF16, split, FP8) at 4096^3, 8192 x 1024 x 4096 and
+           16384 x 64 x 16384: step and kernel time, error on 64 sampled rows.
+peaks      the library's FP32 FMA probe (paired and scalar) with the SM clock during it,
+           and, as context only, PyTorch's BF16 matmul and FP8 scaled matmul at 8192^3.
 precision  8192^3, normal(0,1) and row-scaled by 10^uniform(-3,3): every form's step
            time (FP32 in/out, preparation included), kernel time on prepared operands,
            and relative Frobenius error on 64 sampled rows against the FP64 oracle.
@@ -161,63 +165,81 @@ def grouped(dev, stream):
                        "separate_graph": flops / t_sep_graph / 1e9}}
 
 
-def precision(dev, stream):
+def _forms_at(M, N, K, dist, dev, stream):
+    """Every form at one shape: autotuned program, step time (FP32 in / FP32 out,
+    preparation included), kernel time on prepared operands, and the relative
+    Frobenius error on 64 sampled rows against the FP64 oracle."""
     import torch
-    M = N = K = 8192
     sh = stream.cuda_stream
     out = []
+    A, B = inputs.gemm_operands(M, N, K, seed=0, dist=dist)
+    Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    C = torch.empty(M, N, device=dev)
+    rows = np.linspace(0, M - 1, 64).astype(np.int64)
+    for name, dt in (("f32", pgk.F32), ("bf16", pgk.BF16), ("split", pgk.SPLIT_BF16),
+                     ("fp8", pgk.FP8_E4M3)):
+        cands = [p for p in pgk.default_candidates(dt) if dt != pgk.F32 or p.sr > 1]
+        best, _ = pgk.autotune(Ad, Bd, C, dt, candidates=cands, reps=2, stream=stream)
+        run = lambda: pgk.gemm(Ad, Bd, C, dt, best, stream=sh)
+        run()
+        step_ms = _events_ms(run, 10, stream)
+        err = _rel_err_rows(C, A, B, rows)
+        kern_ms = step_ms
+        pipe = 2.0
+        if dt != pgk.F32:
+            Kp = (K + 15) // 16 * 16
+            if dt == pgk.FP8_E4M3:
+                a = torch.empty(M, Kp, dtype=torch.uint8, device=dev)
+                b = torch.empty(N, Kp, dtype=torch.uint8, device=dev)
+                sa = torch.empty((M + 127) // 128, (K + 127) // 128, device=dev)
+                sb = torch.empty((K + 127) // 128, (N + 127) // 128, device=dev)
+                pgk.quant_fp8(Ad, a, sa, 0, stream=sh)
+                pgk.quant_fp8(Bd, b, sb, 1, stream=sh)
+                k = lambda: pgk.gemm_lowp(M, N, K, dt, a, Kp, b, Kp, C, N, scaleA=sa, scaleB=sb,
+                                          prog=best, stream=sh)
+            elif dt == pgk.BF16:
+                a = torch.empty(M, Kp, dtype=torch.int16, device=dev)
+                b = torch.empty(N, Kp, dtype=torch.int16, device=dev)
+                pgk.cvt_bf16(Ad, a, 0, stream=sh)
+                pgk.cvt_bf16(Bd, b, 1, stream=sh)
+                k = lambda: pgk.gemm_lowp(M, N, K, dt, a, Kp, b, Kp, C, N, prog=best, stream=sh)
+            else:
+                pipe = 6.0
+                a = torch.empty(M, Kp, dtype=torch.int16, device=dev)
+                al = torch.empty_like(a)
+                b = torch.empty(N, Kp, dtype=torch.int16, device=dev)
+                bl = torch.empty_like(b)
+                pgk.split_bf16(Ad, a, al, 0, stream=sh)
+                pgk.split_bf16(Bd, b, bl, 1, stream=sh)
+                k = lambda: pgk.gemm_lowp(M, N, K, dt, a, Kp, b, Kp, C, N, A_lo=al, Bt_lo=bl,
+                                          prog=best, stream=sh)
+            k()
+            kern_ms = _events_ms(k, 10, stream)
+        fl = 2.0 * M * N * K
+        out.append({"shape": [M, N, K], "dist": dist, "form": name, "params": list(best.as_tuple()),
+                    "step_ms": step_ms, "step_tflops": fl / step_ms / 1e9,
+                    "step_gbs_fp32_io": 4.0 * (M * K + K * N + M * N) / step_ms / 1e6,
+                    "kernel_ms": kern_ms, "kernel_pipe_tflops": pipe / 2 * fl / kern_ms / 1e9,
+                    "rel_err_64_rows": err})
+    del Ad, Bd, C
+    torch.cuda.empty_cache()
+    return out
+
+
+def precision(dev, stream):
+    import torch
+    out = []
     for dist in ("normal", "normal_rowscaled"):
-        A, B = inputs.gemm_operands(M, N, K, seed=0, dist=dist)
-        Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
-        C = torch.empty(M, N, device=dev)
-        rows = np.linspace(0, M - 1, 64).astype(np.int64)
-        for name, dt in (("f32", pgk.F32), ("bf16", pgk.BF16), ("split", pgk.SPLIT_BF16),
-                         ("fp8", pgk.FP8_E4M3)):
-            cands = [p for p in pgk.default_candidates(dt) if dt != pgk.F32 or p.sr > 1]
-            best, _ = pgk.autotune(Ad, Bd, C, dt, candidates=cands, reps=2, stream=stream)
-            run = lambda: pgk.gemm(Ad, Bd, C, dt, best, stream=sh)
-            run()
-            step_ms = _events_ms(run, 10, stream)
-            err = _rel_err_rows(C, A, B, rows)
-            kern_ms = step_ms
-            pipe = 2.0
-            if dt != pgk.F32:
-                Kp = (K + 15) // 16 * 16
-                if dt == pgk.FP8_E4M3:
-                    a = torch.empty(M, Kp, dtype=torch.uint8, device=dev)
-                    b = torch.empty(N, Kp, dtype=torch.uint8, device=dev)
-                    sa = torch.empty(M // 128, K // 128, device=dev)
-                    sb = torch.empty(K // 128, N // 128, device=dev)
-                    pgk.quant_fp8(Ad, a, sa, 0, stream=sh)
-                    pgk.quant_fp8(Bd, b, sb, 1, stream=sh)
-                    k = lambda: pgk.gemm_lowp(M, N, K, dt, a, Kp, b, Kp, C, N, scaleA=sa, scaleB=sb,
-                                              prog=best, stream=sh)
-                elif dt == pgk.BF16:
-                    a = torch.empty(M, Kp, dtype=torch.int16, device=dev)
-                    b = torch.empty(N, Kp, dtype=torch.int16, device=dev)
-                    pgk.cvt_bf16(Ad, a, 0, stream=sh)
-                    pgk.cvt_bf16(Bd, b, 1, stream=sh)
-                    k = lambda: pgk.gemm_lowp(M, N, K, dt, a, Kp, b, Kp, C, N, prog=best, stream=sh)
-                else:
-                    pipe = 6.0
-                    a = torch.empty(M, Kp, dtype=torch.int16, device=dev)
-                    al = torch.empty_like(a)
-                    b = torch.empty(N, Kp, dtype=torch.int16, device=dev)
-                    bl = torch.empty_like(b)
-                    pgk.split_bf16(Ad, a, al, 0, stream=sh)
-                    pgk.split_bf16(Bd, b, bl, 1, stream=sh)
-                    k = lambda: pgk.gemm_lowp(M, N, K, dt, a, Kp, b, Kp, C, N, A_lo=al, Bt_lo=bl,
-                                              prog=best, stream=sh)
-                k()
-                kern_ms = _events_ms(k, 10, stream)
-            fl = 2.0 * M * N * K
-            out.append({"dist": dist, "form": name, "params": list(best.as_tuple()),
-                        "step_ms": step_ms, "step_tflops": fl / step_ms / 1e9,
-                        "kernel_ms": kern_ms, "kernel_pipe_tflops": pipe / 2 * fl / kern_ms / 1e9,
-                        "rel_err_64_rows": err})
-        del Ad, Bd, C
-        torch.cuda.empty_cache()
+        out += _forms_at(8192, 8192, 8192, dist, dev, stream)
     return {"config": "precision 8192^3", "results": out}
+
+
+def forms(dev, stream):
+    """Every form at the other FP32 shapes (uniform[-1,1], seeds 0 / 1)."""
+    out = []
+    for M, N, K in ((4096, 4096, 4096), (8192, 1024, 4096), (16384, 64, 16384)):
+        out += _forms_at(M, N, K, "uniform", dev, stream)
+    return {"config": "forms at 4096^3, 8192x1024x4096, 16384x64x16384", "results": out}
 
 
 def mm_table(dev, stream):
@@ -337,6 +359,76 @@ def mlp_kernels(dev, stream):
             "full_gradient_15000_ms": _events_ms(full, 20, stream)}
 
 
+def _clock_sampler():
+    import subprocess
+    try:
+        return subprocess.Popen(["nvidia-smi", "--query-gpu=clocks.sm", "--format=csv,noheader,nounits",
+                                 "-i", "0", "-lms", "100"], stdout=subprocess.PIPE,
+                                stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None
+
+
+def _clock_median(proc):
+    if proc is None:
+        return None
+    proc.terminate()
+    out, _ = proc.communicate(timeout=10)
+    vals = [float(x) for x in out.split() if x.strip().replace(".", "", 1).isdigit()]
+    return statistics.median(vals) if vals else None
+
+
+def peaks(dev, stream):
+    """Measured denominators beside the derived ones.  The FP32 probe is the
+    library's own kernel; the BF16 and FP8 matmuls are PyTorch's (cuBLAS), timed
+    here only as context for the tensor-core fractions."""
+    import torch
+    m = pgk.machine_query(0)
+    blocks = m.sm_count * 8
+    sink = torch.empty(blocks * 256, device=dev)
+    sh = stream.cuda_stream
+    out = {"config": "peaks", "sm_count": m.sm_count}
+    for paired in (1, 0):
+        iters = 20000
+        run = lambda: pgk.simt_peak_probe(blocks, iters, paired, sink, stream=sh)
+        run()
+        clk = _clock_sampler()
+        ms = _events_ms(run, 12, stream)
+        mhz = _clock_median(clk)
+        flops = blocks * 256 * iters * 16 * (2 if paired else 1) * 2
+        r = {"ms": ms, "tflops": flops / ms / 1e9, "sm_mhz": mhz}
+        if mhz:
+            r["tflops_per_ghz"] = r["tflops"] / (mhz / 1e3)
+            r["derived_at_clock"] = m.sm_count * 128 * 2 * mhz * 1e6 / 1e12
+        out["fma_probe_paired" if paired else "fma_probe_scalar"] = r
+    n = 8192
+    flops = 2.0 * n * n * n
+    try:
+        a = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
+        b = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
+        run = lambda: torch.matmul(a, b)
+        for _ in range(3):
+            run()
+        clk = _clock_sampler()
+        ms = _events_ms(run, 20, stream)
+        out["torch_bf16_matmul"] = {"ms": ms, "tflops": flops / ms / 1e9, "sm_mhz": _clock_median(clk)}
+    except Exception as e:  # context only
+        out["torch_bf16_matmul"] = {"error": str(e)[:200]}
+    try:
+        a8 = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn)
+        b8 = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device=dev)
+        run = lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        for _ in range(3):
+            run()
+        clk = _clock_sampler()
+        ms = _events_ms(run, 20, stream)
+        out["torch_fp8_scaled_mm"] = {"ms": ms, "tflops": flops / ms / 1e9, "sm_mhz": _clock_median(clk)}
+    except Exception as e:  # context only
+        out["torch_fp8_scaled_mm"] = {"error": str(e)[:200]}
+    return out
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
@@ -349,7 +441,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     fns = {"config1": config1, "scale": scale, "grouped": grouped, "precision": precision,
            "mm": mm_table, "transpose": transpose_table, "jacobi": jacobi_table,
-           "errmeas": errmeas, "mlp": mlp_kernels}
+           "errmeas": errmeas, "mlp": mlp_kernels, "peaks": peaks, "forms": forms}
     for w in args.which:
         t0 = time.time()
         with torch.cuda.stream(stream):

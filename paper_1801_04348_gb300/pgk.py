@@ -97,6 +97,7 @@ _SIGS = {
     "pgk_gemm_lowp": (_i, [_i, _i, _i, _i, _p, _i, _p, _i, _p, _p, _p, _p, _p, _i, _i,
                            ctypes.POINTER(Params), _p]),
     "pgk_relerr": (_i, [_i, _i, _p, _i, _p, _i, _p, _p, _p]),
+    "pgk_simt_peak_probe": (_i, [_i, _i, _i, _p, _p]),
     "pgk_mlp_forward": (_i, [_i, _p, _p, _p, _p]),
     "pgk_mlp_loss_grad": (_i, [_i, _p, _p, _p, _p, _p, _p, _p]),
     "pgk_mlp_loss_grad_noalloc": (_i, [_i, _p, _p, _p, _p, _p, _p, _p]),
@@ -349,6 +350,12 @@ def relerr(C, Cref, out, row_index=None, stream=None, rows=None, cols=None):
     cols = Cref.shape[1] if cols is None else cols
     _check(lib().pgk_relerr(rows, cols, _ptr(C), C.stride(0), _ptr(Cref), Cref.stride(0),
                             _ptr(row_index), _ptr(out), _stream(stream)), "pgk_relerr")
+
+
+def simt_peak_probe(blocks, iters, paired, sink, stream=None):
+    """FP32 FMA throughput probe; flops = blocks * 256 * iters * 16 * (2 if paired else 1) * 2."""
+    _check(lib().pgk_simt_peak_probe(int(blocks), int(iters), int(paired), _ptr(sink), _stream(stream)),
+           "pgk_simt_peak_probe")
 
 
 # ------------------------------------------------------------- cost model

@@ -65,3 +65,4 @@ def test_invalid_arguments_are_errors_not_crashes(L):
     assert st == 3  # UNSUPPORTED: no such register-blocked variant
     assert L.pgk_gemm(0, 1, 1, 0, None, 1, None, 1, None, 1, 0, None, None) == 1
     assert L.pgk_cvt_bf16(0, 1, None, 1, None, 1, 0, None) == 1
+    assert L.pgk_simt_peak_probe(0, 1, 1, None, None) == 1

@@ -175,3 +175,22 @@ def test_split_k_exact_on_integers(dev, M, N, K):
     for prog in _all_simt_params():
         if prog.sr > 1:
             assert np.array_equal(_run(dev, A, B, prog).astype(np.float64), ref), prog.as_tuple()
+
+
+@pytest.mark.parametrize("paired", [1, 0])
+def test_fma_probe_below_the_derived_peak(dev, machine, paired):
+    """The FFMA probe cannot beat SM count x 128 lanes x 2 flop x the maximum SM
+    clock, and a dependency-free FMA stream should come close to it."""
+    blocks, iters = machine.sm_count * 8, 4000
+    sink = torch.empty(blocks * 256, device=dev)
+    pgk.simt_peak_probe(blocks, iters, paired, sink)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    pgk.simt_peak_probe(blocks, iters, paired, sink)
+    b.record()
+    b.synchronize()
+    tflops = blocks * 256 * iters * 16 * (2 if paired else 1) * 2 / a.elapsed_time(b) / 1e9
+    peak = machine.sm_count * 128 * 2 * 2.1e9 / 1e12  # TFLOP/s; 2100 MHz bounds the 2070 MHz maximum
+    assert 0.3 * peak < tflops < peak
+    assert torch.isfinite(sink).all()
