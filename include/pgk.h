@@ -208,6 +208,30 @@ PGK_API pgk_status pgk_gemm(int M, int N, int K, pgk_dtype dtype, const float* A
                     const float* B, int ldb, float* C, int ldc, int beta,
                     const pgk_params* prog, void* stream);
 
+/* GEMM on host buffers: C = A B (beta = 0) or C += A B (beta = 1) with A, B and
+ * C in host memory, row-major FP32 as for pgk_gemm (dtype selects the form,
+ * prog = NULL picks the tuned program).  An extension of the method for callers
+ * whose operands live in host memory; the paper's kernels read device memory only.
+ * The library copies A and B into one of two device buffer sets that it owns,
+ * on a stream of its own, then runs the GEMM on `stream`; consecutive calls
+ * alternate the sets, so the input copies of one call run while the GEMM of the
+ * previous call computes.  The GEMM runs in two row panels (the first ending on a
+ * multiple of 128 rows; the tensor-core forms convert B once) into a device
+ * buffer; the first panel's C is copied back on a second library stream while
+ * the second panel computes, and `stream` waits for both copies.  Pinned
+ * buffers (cudaHostAlloc / cudaMallocHost / cudaHostRegister) copy at the host
+ * link's full rate; pageable memory works but the driver stages it.
+ * Ordering: the input copies are not ordered after work enqueued on `stream`
+ * before the call; A and B must hold their values, and C must not be accessed,
+ * from the call until `stream` has completed the work it enqueued.  C is then in
+ * host memory.  The buffer sets grow to the largest call and are freed by
+ * pgk_shutdown().  Calls from several host threads are serialised.
+ * Errors: INVALID_ARG (also for device or managed pointers), NO_MEMORY, and
+ * those of pgk_gemm. */
+PGK_API pgk_status pgk_gemm_host(int M, int N, int K, pgk_dtype dtype, const float* A, int lda,
+                                 const float* B, int ldb, float* C, int ldc, int beta,
+                                 const pgk_params* prog, void* stream);
+
 /* C = A*B (beta = 0) or C += A*B (beta = 1) on int32 matrices, modulo 2^32:
  * the paper's own data type (Fig. "cudamul").  Same case discussion, variants
  * and errors as pgk_gemm with dtype PGK_I32 (SIMT only). */

@@ -416,8 +416,31 @@ using namespace pgk;
 namespace pgk {
 pgk_status tc_gemm_fp32_inputs(const pgk_case& c, int M, int N, int K, pgk_dtype dtype,
                                const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                               int beta, cudaStream_t st);
+                               int beta, cudaStream_t st, bool prep_b);
+
+pgk_status gemm_device(int M, int N, int K, pgk_dtype dtype, const float* A, int lda, const float* B,
+                       int ldb, float* C, int ldc, int beta, const pgk_params* prog, cudaStream_t stream,
+                       bool reuse_b) {
+    pgk_status st = check_gemm_args(M, N, K, A, lda, B, ldb, C, ldc);
+    if (st != PGK_OK) return st;
+    pgk_machine m;
+    st = current_machine(&m, NULL);
+    if (st != PGK_OK) return st;
+    pgk_params p;
+    if (prog) {
+        p = *prog;
+    } else if (pgk_tune_cache_get(M, N, K, dtype, &p) != PGK_OK &&
+               learned_select(M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, stream, &p) != PGK_OK) {
+        p = default_params(M, N, K, dtype);
+    }
+    pgk_case c;
+    st = select_any(&m, NULL, M, N, K, dtype, &p, &c);
+    if (st != PGK_OK) return st;
+    if (dtype == PGK_F32 || dtype == PGK_I32)
+        return run_simt_case(c, M, N, K, A, lda, B, ldb, C, ldc, beta, stream);
+    return tc_gemm_fp32_inputs(c, M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, stream, !reuse_b);
 }
+}  // namespace pgk
 
 extern "C" {
 
@@ -503,26 +526,8 @@ pgk_status pgk_gemm_case(const pgk_case* c, int M, int N, int K, const float* A,
 
 pgk_status pgk_gemm(int M, int N, int K, pgk_dtype dtype, const float* A, int lda, const float* B,
                     int ldb, float* C, int ldc, int beta, const pgk_params* prog, void* stream) {
-    pgk_status st = check_gemm_args(M, N, K, A, lda, B, ldb, C, ldc);
-    if (st != PGK_OK) return st;
-    pgk_machine m;
-    st = current_machine(&m, NULL);
-    if (st != PGK_OK) return st;
-    pgk_params p;
-    if (prog) {
-        p = *prog;
-    } else if (pgk_tune_cache_get(M, N, K, dtype, &p) != PGK_OK &&
-               learned_select(M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, (cudaStream_t)stream,
-                              &p) != PGK_OK) {
-        p = default_params(M, N, K, dtype);
-    }
-    pgk_case c;
-    st = select_any(&m, NULL, M, N, K, dtype, &p, &c);
-    if (st != PGK_OK) return st;
-    if (dtype == PGK_F32 || dtype == PGK_I32)
-        return run_simt_case(c, M, N, K, A, lda, B, ldb, C, ldc, beta, (cudaStream_t)stream);
-    return tc_gemm_fp32_inputs(c, M, N, K, dtype, A, lda, B, ldb, C, ldc, beta,
-                               (cudaStream_t)stream);
+    return gemm_device(M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, prog, (cudaStream_t)stream,
+                       false);
 }
 
 pgk_status pgk_gemm_i32(int M, int N, int K, const int32_t* A, int lda, const int32_t* B, int ldb,
@@ -536,6 +541,7 @@ pgk_status pgk_gemm_i32(int M, int N, int K, const int32_t* A, int lda, const in
 pgk_status pgk_shutdown(void) {
     costmodel_release();
     grouped_release();
+    hostio_release();
     tune_cache_release();
     free_workspaces();
     return PGK_OK;

@@ -88,6 +88,12 @@ pgk_status tc_gemm_launch(const pgk_case& c, int M, int N, int K, pgk_dtype dtyp
 
 // ------------------------------------------------------------- grouped
 void grouped_release();
+void hostio_release();
+// pgk_gemm; with reuse_b the tensor-core forms keep the converted B of the
+// previous call on the same stream (same B, N and K) instead of converting it again.
+pgk_status gemm_device(int M, int N, int K, pgk_dtype dtype, const float* A, int lda, const float* B,
+                       int ldb, float* C, int ldc, int beta, const pgk_params* prog, cudaStream_t stream,
+                       bool reuse_b);
 void tune_cache_release();
 void costmodel_release();
 // Learned selection for pgk_gemm(prog = NULL) on a tuning-cache miss (misc.cu).

@@ -861,7 +861,7 @@ pgk_status launch_quant_fp8(int rows, int cols, const float* src, int lds, uint8
 // -> tensor-core kernel.
 pgk_status tc_gemm_fp32_inputs(const pgk_case& c, int M, int N, int K, pgk_dtype dtype,
                                const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                               int beta, cudaStream_t s) {
+                               int beta, cudaStream_t s, bool prep_b) {
     const int Kp = (K + 15) / 16 * 16;
     const int esz = dtype == PGK_FP8_E4M3 ? 1 : 2;
     pgk_status st;
@@ -871,7 +871,7 @@ pgk_status tc_gemm_fp32_inputs(const pgk_case& c, int M, int N, int K, pgk_dtype
     if (!b0) return st;
     if (dtype == PGK_BF16) {
         if ((st = launch_cvt_bf16(M, K, A, lda, (uint16_t*)a0, Kp, 0, s)) != PGK_OK) return st;
-        if ((st = launch_cvt_bf16(K, N, B, ldb, (uint16_t*)b0, Kp, 1, s)) != PGK_OK) return st;
+        if (prep_b && (st = launch_cvt_bf16(K, N, B, ldb, (uint16_t*)b0, Kp, 1, s)) != PGK_OK) return st;
         return tc_gemm_launch(c, M, N, K, dtype, a0, Kp, b0, Kp, nullptr, nullptr, nullptr, nullptr,
                               C, ldc, beta, s);
     }
@@ -882,7 +882,8 @@ pgk_status tc_gemm_fp32_inputs(const pgk_case& c, int M, int N, int K, pgk_dtype
         if (!b1) return st;
         if ((st = launch_split_bf16(M, K, A, lda, (uint16_t*)a0, (uint16_t*)a1, Kp, 0, s)) != PGK_OK)
             return st;
-        if ((st = launch_split_bf16(K, N, B, ldb, (uint16_t*)b0, (uint16_t*)b1, Kp, 1, s)) != PGK_OK)
+        if (prep_b &&
+            (st = launch_split_bf16(K, N, B, ldb, (uint16_t*)b0, (uint16_t*)b1, Kp, 1, s)) != PGK_OK)
             return st;
         return tc_gemm_launch(c, M, N, K, dtype, a0, Kp, b0, Kp, a1, b1, nullptr, nullptr, C, ldc,
                               beta, s);
@@ -893,7 +894,8 @@ pgk_status tc_gemm_fp32_inputs(const pgk_case& c, int M, int N, int K, pgk_dtype
     float* sb = (float*)workspace(WS_SB, (size_t)kt * nt * 4, &st);
     if (!sb) return st;
     if ((st = launch_quant_fp8(M, K, A, lda, (uint8_t*)a0, Kp, sa, kt, 0, s)) != PGK_OK) return st;
-    if ((st = launch_quant_fp8(K, N, B, ldb, (uint8_t*)b0, Kp, sb, nt, 1, s)) != PGK_OK) return st;
+    if (prep_b && (st = launch_quant_fp8(K, N, B, ldb, (uint8_t*)b0, Kp, sb, nt, 1, s)) != PGK_OK)
+        return st;
     return tc_gemm_launch(c, M, N, K, dtype, a0, Kp, b0, Kp, nullptr, nullptr, sa, sb, C, ldc, beta,
                           s);
 }

@@ -96,6 +96,7 @@ _SIGS = {
     "pgk_quant_fp8": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _i, _p]),
     "pgk_gemm_lowp": (_i, [_i, _i, _i, _i, _p, _i, _p, _i, _p, _p, _p, _p, _p, _i, _i,
                            ctypes.POINTER(Params), _p]),
+    "pgk_gemm_host": (_i, [_i, _i, _i, _i, _p, _i, _p, _i, _p, _i, _i, ctypes.POINTER(Params), _p]),
     "pgk_relerr": (_i, [_i, _i, _p, _i, _p, _i, _p, _p, _p]),
     "pgk_simt_peak_probe": (_i, [_i, _i, _i, _p, _p]),
     "pgk_mlp_forward": (_i, [_i, _p, _p, _p, _p]),
@@ -219,6 +220,18 @@ def gemm(A, B, C, dtype=F32, prog: Params | None = None, beta=0, stream=None, M=
     st = lib().pgk_gemm(M, N, K, dtype, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, int(beta),
                         ctypes.byref(prog) if prog is not None else None, _stream(stream))
     _check(st, "pgk_gemm")
+
+
+def gemm_host(A, B, C, dtype=F32, prog: Params | None = None, beta=0, stream=None):
+    """GEMM on host (CPU) FP32 tensors, pinned for full copy rate; asynchronous on
+    `stream`: A and B must keep their values and C must not be read until the
+    stream has completed the call."""
+    M, K = A.shape
+    N = B.shape[1]
+    st = lib().pgk_gemm_host(M, N, K, dtype, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C),
+                             C.stride(0), int(beta), ctypes.byref(prog) if prog is not None else None,
+                             _stream(stream))
+    _check(st, "pgk_gemm_host")
 
 
 def gemm_i32(A, B, C, prog: Params | None = None, beta=0, stream=None):

@@ -66,3 +66,4 @@ def test_invalid_arguments_are_errors_not_crashes(L):
     assert L.pgk_gemm(0, 1, 1, 0, None, 1, None, 1, None, 1, 0, None, None) == 1
     assert L.pgk_cvt_bf16(0, 1, None, 1, None, 1, 0, None) == 1
     assert L.pgk_simt_peak_probe(0, 1, 1, None, None) == 1
+    assert L.pgk_gemm_host(0, 1, 1, 0, None, 1, None, 1, None, 1, 0, None, None) == 1
