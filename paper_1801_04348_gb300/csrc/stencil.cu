@@ -56,12 +56,16 @@ __global__ void k_transpose_cached(TArgs p) {
     }
     __syncthreads();
     // output row c0 + j holds elements r0 .. r0 + B0 - 1: consecutive threads write
-    // consecutive elements of one output row
-    const int tid = u0 * B1 + u1, nt = B0 * B1;
-    for (int idx = tid; idx < B0 * W; idx += nt) {
-        const int j = idx / B0, i = idx - j * B0;
-        if (c0 + j < p.cols && r0 + i < p.rows)
-            p.dst[(size_t)(c0 + j) * p.ldd + r0 + i] = tile_t[i * P + j];
+    // consecutive elements of one output row.  Thread t writes element i = t mod B0
+    // of output rows j = t div B0 + m B1 (m = 0 .. S - 1): one division per thread
+    const int tid = u0 * B1 + u1;
+    const int i = tid % B0, j0 = tid / B0;
+    if (r0 + i < p.rows) {
+#pragma unroll
+        for (int m = 0; m < S; ++m) {
+            const int j = j0 + m * B1;
+            if (c0 + j < p.cols) p.dst[(size_t)(c0 + j) * p.ldd + r0 + i] = tile_t[i * P + j];
+        }
     }
 }
 

@@ -24,6 +24,9 @@ precision  8192^3, normal(0,1) and row-scaled by 10^uniform(-3,3): every form's 
            time (FP32 in/out, preparation included), kernel time on prepared operands,
            and relative Frobenius error on 64 sampled rows against the FP64 oracle.
 
+--only B0,B1,s[,sr,tile] restricts mm (n = 2^11), transpose and jacobi (2^27 + 2 points) to
+one program point, for profiling a single kernel.
+
 Timing: CUDA events on the launching stream after warm-up; medians of repeated runs.
 The oracle is only used for the error columns (test infrastructure).
 """
@@ -40,6 +43,7 @@ import numpy as np
 from . import inputs, pgk
 
 PEAK_MHZ = 2070.0
+ONLY = None   # --only B0,B1,s: run a single program point of mm / transpose / jacobi (profiling)
 
 
 def _events_ms(fn, reps, stream):
@@ -251,19 +255,24 @@ def mm_table(dev, stream):
     rng = np.random.default_rng(0)
     out = []
     sh = stream.cuda_stream
-    for n in (1024, 2048):
+    if ONLY is not None:
+        grid = [(ONLY[1], ONLY[0])]
+    for n in ((2048,) if ONLY is not None else (1024, 2048)):
         A = torch.from_numpy(rng.integers(-100, 100, size=(n, n)).astype(np.int32)).to(dev)
         B = torch.from_numpy(rng.integers(-100, 100, size=(n, n)).astype(np.int32)).to(dev)
         C = torch.empty(n, n, dtype=torch.int32, device=dev)
         rows = []
         for ub1, b0 in grid:
-            for s in (2, 4):
-                p = pgk.params(b0, ub1, s)
+            for s in ((ONLY[2],) if ONLY is not None else (2, 4)):
+                p = pgk.params(*ONLY) if ONLY is not None else pgk.params(b0, ub1, s)
                 run = lambda: pgk.gemm_i32(A, B, C, p, stream=sh)
                 run()
                 ms = _events_ms(run, 10, stream)
                 rows.append({"ub1": ub1, "B0": b0, "s": s, "ms": ms, "gops": 2.0 * n ** 3 / ms / 1e6})
         best = min(rows, key=lambda r: r["ms"])
+        if ONLY is not None:
+            out.append({"n": n, "paper_grid": rows})
+            continue
         cands = pgk.default_candidates(pgk.I32)
         tuned, _ = pgk.autotune(A, B, C, pgk.I32, candidates=[c for c in cands if c.sr > 1], reps=3,
                                 stream=stream)
@@ -286,8 +295,8 @@ def transpose_table(dev, stream):
     c = torch.empty(n, n, dtype=torch.int32, device=dev)
     sh = stream.cuda_stream
     rows = []
-    for b0, b1 in ((4, 32), (8, 32), (16, 32), (32, 32)):
-        for s in (2, 4, 8):
+    for b0, b1 in ([tuple(ONLY[:2])] if ONLY is not None else ((4, 32), (8, 32), (16, 32), (32, 32))):
+        for s in ((ONLY[2],) if ONLY is not None else (2, 4, 8)):
             p = pgk.params(b0, b1, s)
             run = lambda: pgk.transpose(a, c, p, stream=sh)
             run()
@@ -304,11 +313,11 @@ def jacobi_table(dev, stream):
     import torch
     out = {}
     sh = stream.cuda_stream
-    for n, steps in ((2 ** 15 + 2, 4), (2 ** 27 + 2, 4)):
+    for n, steps in (((2 ** 27 + 2, 4),) if ONLY is not None else ((2 ** 15 + 2, 4), (2 ** 27 + 2, 4))):
         a = torch.randint(-2 ** 20, 2 ** 20, (2 * n,), dtype=torch.int32, device=dev)
         rows = []
-        for b in (16, 32, 64, 128, 256):
-            for s in (2, 4, 8):
+        for b in ((ONLY[0],) if ONLY is not None else (16, 32, 64, 128, 256)):
+            for s in ((ONLY[2],) if ONLY is not None else (2, 4, 8)):
                 p = pgk.params(b, 1, s)
                 run = lambda: pgk.jacobi(a, n, steps, p, stream=sh)
                 run()
@@ -434,7 +443,12 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
     ap.add_argument("which", nargs="*", default=["config1", "scale", "grouped", "precision"])
+    ap.add_argument("--only", default=None,
+                    help="B0,B1,s[,sr,tile]: one program point of mm / transpose / jacobi (profiling)")
     args = ap.parse_args()
+    global ONLY
+    if args.only:
+        ONLY = [int(x) for x in args.only.split(",")]
     os.makedirs(args.out, exist_ok=True)
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
