@@ -51,7 +51,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampling every 200 ms while the timed region runs."""
+    """nvidia-smi sampling every 50 ms while the timed region runs."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -470,7 +470,7 @@ def roofline(form, alg, gemm_ms, step_ms, machine, pk, pk_src, clocks, traffic=N
     kind = "sustained" if sustained else "burst"
     mult = 2.0 if form == "fp8" else 1.0
     peak = mult * base
-    src = (f"{'2 x ' if form == 'fp8' else ''}bf16 {kind} ({pk_src}, timed region {timed_s:.1f} s)"
+    src = (f"{'2 x ' if form == 'fp8' else ''}bf16 {kind} ({pk_src}, timed region {timed_s:.3f} s)"
            + ("; FP8 dense = 2x BF16 nominal" if form == "fp8" else ""))
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": "k_tc_gemm (tcgen05)",
@@ -504,7 +504,8 @@ def measure_e2e(form, prog, A, B, M, N, K, dev, stream, pgk, torch, args, ws):
             "h2d_bytes_per_step": (M * K + K * N) * 4, "d2h_bytes_per_step": M * N * 4,
             "steps": steps, "ms_per_step": ms, "api": "pgk_gemm_host (pinned host A, B, C)",
             "pipelining": "input copies of step i+1 on the library's stream overlap the GEMM of step i; "
-                          "C written into mapped host memory by the GEMM",
+                          "the GEMM runs in two row panels and the first panel's C is copied back "
+                          "while the second computes",
             "timing": "host clock, device idle before the first call, synchronised after the last"}
 
 
