@@ -100,3 +100,50 @@ def test_jacobi_every_leaf(dev):
             torch.cuda.synchronize()
             assert np.array_equal(ad.cpu().numpy(), ref)
     assert seen == {0, 1, 2}
+
+
+def test_transpose_order_2e14_sampled_rows(dev):
+    """The timed workload (order 2^14, every point of the paper's grid): sampled rows
+    of the transpose are the matching columns of the input, bit for bit."""
+    n = 16384
+    g = torch.Generator(device="cpu").manual_seed(14)
+    a = torch.randint(-2 ** 31, 2 ** 31 - 1, (n, n), dtype=torch.int32, generator=g).to(dev)
+    c = torch.empty(n, n, dtype=torch.int32, device=dev)
+    rows = torch.from_numpy(np.r_[0, 1, np.linspace(2, n - 2, 30).astype(np.int64), n - 1]).to(dev)
+    want = a[:, rows].t().cpu().numpy()
+    for b0, b1 in TABLE_BLOCKS:
+        for s in (2, 4, 8):
+            c.fill_(-1)
+            pgk.transpose(a, c, pgk.params(b0, b1, s))
+            torch.cuda.synchronize()
+            assert np.array_equal(c[rows].cpu().numpy(), want), (b0, b1, s)
+
+
+def test_jacobi_2e27_windows(dev):
+    """The timed workload (2^27 + 2 points, T = 4, every block and granularity of the
+    grid at full size) against the oracle on windows: after T steps a point depends
+    on the T points either side, so the oracle run on a window is exact everywhere
+    but within T + 1 points of a cut that is not the array's own end."""
+    n, steps = 2 ** 27 + 2, 4
+    a = _jacobi_input(n, 27)
+    starts = np.r_[0, np.linspace(5000, n - 5000, 14).astype(np.int64), n - 2048]
+    refs = []
+    for lo in starts:
+        hi = min(lo + 2048, n)
+        m = hi - lo
+        sub = np.concatenate([a[lo:hi], a[n + lo:n + hi]])
+        r = stencil.jacobi(sub, m, steps)
+        v0 = 0 if lo == 0 else steps + 1
+        v1 = m if hi == n else m - steps - 1
+        refs.append((lo, v0, v1, r[v0:v1], r[m + v0:m + v1]))
+    ad0 = torch.from_numpy(a).to(dev)
+    for b in (16, 64, 128, 256):
+        for s in (2, 8):
+            ad = ad0.clone()
+            pgk.jacobi(ad, n, steps, pgk.params(b, 1, s))
+            torch.cuda.synchronize()
+            for lo, v0, v1, r_first, r_second in refs:
+                first = ad[lo + v0:lo + v1].cpu().numpy()
+                second = ad[n + lo + v0:n + lo + v1].cpu().numpy()
+                assert np.array_equal(first, r_first), (b, s, lo)
+                assert np.array_equal(second, r_second), (b, s, lo)
