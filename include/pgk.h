@@ -246,15 +246,25 @@ PGK_API pgk_status pgk_gemm_i32(int M, int N, int K, const int32_t* A, int lda, 
 PGK_API pgk_status pgk_gemm_case(const pgk_case* c, int M, int N, int K, const float* A, int lda,
                          const float* B, int ldb, float* C, int ldc, int beta, void* stream);
 
-/* G independent FP32 GEMMs C_g = A_g * B_g in ONE persistent launch: the host
- * packs the problems (host array `problems`, device matrix pointers) and the
- * tile prefix sums into a device table; every CTA pulls (problem, tile) work
- * items from an atomic counter until all tiles are done.  `prog` selects the
- * register-blocked tile variant (NULL = tuned/default).  use_graph = 1 captures
- * the counter reset and the launch in a CUDA graph, cached per problem set and
- * replayed on later calls with the same problems.
- * Errors: INVALID_ARG (G < 1, a bad problem), UNSUPPORTED (not F32 / variant),
- * CUDA, NO_MEMORY. */
+/* G independent GEMMs C_g = A_g * B_g (C_g += with beta = 1) on FP32 operands.
+ * An extension of the method (batching), not in the paper.
+ * PGK_F32: ONE persistent launch: the host packs the problems (host array
+ * `problems`, device matrix pointers) and the tile prefix sums into a device
+ * table; every CTA pulls (problem, tile) work items from an atomic counter
+ * until all tiles are done.  `prog` selects the register-blocked tile variant
+ * (NULL = tuned/default).  use_graph = 1 captures the counter reset and the
+ * launch in a CUDA graph, cached per problem set and replayed on later calls
+ * with the same problems.
+ * PGK_BF16 / PGK_SPLIT_BF16: three launches on `stream`: one converts every A_g,
+ * one every B_g (transposed), into library workspaces packed problem after
+ * problem (each at a multiple of 128 rows, K zero-padded to a multiple of 64),
+ * and one persistent tensor-core launch runs the tiles of all problems, in
+ * decreasing K order.  Each C_g equals, bit for bit, pgk_gemm on that problem
+ * with the same tile program.  `prog` = (128, 128, stages, 0, 64): stages 6
+ * for BF16, 3 (split) or 6 (split in three passes); NULL = the first.
+ * use_graph does not apply.  No alignment condition on the problems.
+ * Errors: INVALID_ARG (G < 1, a bad problem, a set too large for one launch),
+ * UNSUPPORTED (FP8 / no such variant), CUDA, NO_MEMORY. */
 PGK_API pgk_status pgk_gemm_grouped(int G, const pgk_problem* problems, pgk_dtype dtype,
                             const pgk_params* prog, int use_graph, int beta, void* stream);
 

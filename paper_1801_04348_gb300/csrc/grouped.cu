@@ -228,12 +228,14 @@ using namespace pgk;
 extern "C" pgk_status pgk_gemm_grouped(int G, const pgk_problem* problems, pgk_dtype dtype,
                                        const pgk_params* prog, int use_graph, int beta,
                                        void* stream) {
-    if (dtype != PGK_F32) {
-        set_error("the grouped GEMM runs the FP32 SIMT family");
-        return PGK_ERR_UNSUPPORTED;
-    }
     pgk_status st = check_problems(G, problems);
     if (st != PGK_OK) return st;
+    if (dtype == PGK_BF16 || dtype == PGK_SPLIT_BF16)
+        return tc_gemm_grouped(G, problems, dtype, prog, beta, (cudaStream_t)stream);
+    if (dtype != PGK_F32) {
+        set_error("the grouped GEMM runs the FP32 SIMT family and the BF16 / split-BF16 forms");
+        return PGK_ERR_UNSUPPORTED;
+    }
     pgk_params p;
     if (prog) {
         p = *prog;

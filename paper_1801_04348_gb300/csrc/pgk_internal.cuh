@@ -89,6 +89,24 @@ pgk_status tc_gemm_launch(const pgk_case& c, int M, int N, int K, pgk_dtype dtyp
 // ------------------------------------------------------------- grouped
 void grouped_release();
 void hostio_release();
+
+// One problem of a grouped operand conversion (see k_cvt_grouped in prep.cu).
+struct GCvt {
+    const float* src;
+    int lds, rows, cols;
+    int width;          // converted width: the padded K (a multiple of 64)
+    int vec;            // src 16-byte aligned with lds a multiple of 4
+    int pad;
+    long long dst_row;  // first destination row in the packed workspace
+};
+// Grouped GEMM in the BF16 or split form (tc_gemm.cu); the compiled grouped tile
+// variants of a form as (128, B1, stages, 0, 64).
+pgk_status tc_gemm_grouped(int G, const pgk_problem* pr, pgk_dtype dtype, const pgk_params* prog,
+                           int beta, cudaStream_t s);
+int tc_grouped_variants(pgk_dtype dtype, pgk_params* out, int cap);
+// mode 0: BF16, mode 1: hi/lo split.  total = prefix[G] tile items.
+pgk_status launch_cvt_grouped(int mode, int transpose, const GCvt* probs, const int* prefix, int G,
+                              int total, uint16_t* d0, uint16_t* d1, long long ldd, cudaStream_t st);
 // pgk_gemm; with reuse_b the tensor-core forms keep the converted B of the
 // previous call on the same stream (same B, N and K) instead of converting it again.
 pgk_status gemm_device(int M, int N, int K, pgk_dtype dtype, const float* A, int lda, const float* B,

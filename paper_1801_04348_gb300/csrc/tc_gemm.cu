@@ -25,7 +25,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
+#include <vector>
 
 #include "pgk_internal.cuh"
 
@@ -230,6 +232,15 @@ __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// One problem of a grouped launch: its sizes, the first rows of its operands in
+// the packed workspaces (A: M rows, B^T: N rows, both K-major with zeros from K
+// to the next multiple of the K block) and its output.
+struct TcProb {
+    float* C;
+    int M, N, K, ldc;
+    int rowA, rowB;
+};
+
 struct TcParams {
     int M, N, K;
     float* C;
@@ -238,9 +249,13 @@ struct TcParams {
     const float* sA;   // FP8: ceil(M/128) x ceil(K/128)
     const float* sB;   // FP8: ceil(K/128) x ceil(N/128)
     unsigned int* err;
+    // grouped launch: tile t is (problem, tile row, tile column) = gtiles[t].x, .y, .z
+    const int4* gtiles;
+    const TcProb* gprobs;
+    int ntiles_g;
 };
 
-template <class Cfg>
+template <class Cfg, bool GROUPED = false>
 __global__ void __launch_bounds__(Cfg::THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
@@ -259,9 +274,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
 
+    static_assert(!(GROUPED && Cfg::MODE == MODE_FP8), "grouped launches take BF16 or split operands");
     const int tiles_m = (p.M + Cfg::BM - 1) / Cfg::BM;
     const int tiles_n = (p.N + Cfg::BN - 1) / Cfg::BN;
-    const int ntiles = tiles_m * tiles_n;
+    const int ntiles = GROUPED ? p.ntiles_g : tiles_m * tiles_n;
     const int nkb = (p.K + Cfg::BK - 1) / Cfg::BK;
 
     if (threadIdx.x == 0) {
@@ -307,6 +323,38 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         tm = first + r % gm;
         tn = r / gm;
     };
+    // everything a warp needs about tile t: its position, its problem's sizes and
+    // output, and where its operands start in the packed workspaces (grouped)
+    struct TileInfo {
+        int tm, tn, M, N, nkb, rowA, rowB, ldc;
+        float* C;
+    };
+    auto tile_info = [&](int t) {
+        TileInfo ti;
+        if (GROUPED) {
+            const int4 d = __ldg(p.gtiles + t);
+            const TcProb* q = p.gprobs + d.x;
+            ti.tm = d.y;
+            ti.tn = d.z;
+            ti.M = q->M;
+            ti.N = q->N;
+            ti.nkb = (q->K + Cfg::BK - 1) / Cfg::BK;
+            ti.rowA = q->rowA;
+            ti.rowB = q->rowB;
+            ti.ldc = q->ldc;
+            ti.C = q->C;
+        } else {
+            coords(t, ti.tm, ti.tn);
+            ti.M = p.M;
+            ti.N = p.N;
+            ti.nkb = nkb;
+            ti.rowA = 0;
+            ti.rowB = 0;
+            ti.ldc = p.ldc;
+            ti.C = p.C;
+        }
+        return ti;
+    };
 
     if (warp == 0) {
         // ------------------------------------------------------- producer
@@ -316,9 +364,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             uint32_t issued_mask = 0, last_parity = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                int tm, tn;
-                coords(t, tm, tn);
-                for (int kb = 0; kb < nkb && ok; ++kb)
+                const TileInfo ti = tile_info(t);
+                const int ya = ti.rowA + ti.tm * Cfg::BM, yb = ti.rowB + ti.tn * Cfg::BN;
+                for (int kb = 0; kb < ti.nkb && ok; ++kb)
                 for (int v = 0; v < Cfg::PASSES; ++v) {
                     if (!mbar_wait(&empty_bar[stage], phase ^ 1u, abort_flag, p.err,
                                    ERR_TIMEOUT_PRODUCER)) {
@@ -331,13 +379,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     // passes of MODE_SPLIT3: 0 = (A lo, B hi), 1 = (A hi, B lo), 2 = (A hi, B hi)
                     const CUtensorMap* ma = (Cfg::MODE == MODE_SPLIT3 && v == 0) ? &tmA2 : &tmA;
                     const CUtensorMap* mb = (Cfg::MODE == MODE_SPLIT3 && v == 1) ? &tmB2 : &tmB;
-                    tma_load_2d(st, ma, &full_bar[stage], x, tm * Cfg::BM);
-                    tma_load_2d(st + Cfg::A_BYTES, mb, &full_bar[stage], x, tn * Cfg::BN);
+                    tma_load_2d(st, ma, &full_bar[stage], x, ya);
+                    tma_load_2d(st + Cfg::A_BYTES, mb, &full_bar[stage], x, yb);
                     if (Cfg::MODE == MODE_SPLIT) {
-                        tma_load_2d(st + Cfg::A_BYTES + Cfg::B_BYTES, &tmA2, &full_bar[stage], x,
-                                    tm * Cfg::BM);
+                        tma_load_2d(st + Cfg::A_BYTES + Cfg::B_BYTES, &tmA2, &full_bar[stage], x, ya);
                         tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tmB2, &full_bar[stage],
-                                    x, tn * Cfg::BN);
+                                    x, yb);
                     }
                     issued_mask |= 1u << stage;
                     last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
@@ -373,6 +420,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             bool ok = true;
             bool issued_any = false;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int tnkb = GROUPED ? tile_info(t).nkb : nkb;
                 if (Cfg::CHUNK == 0) {
                     if (!mbar_wait(&acce_bar[acc], acc_phase ^ 1u, abort_flag, p.err, ERR_TIMEOUT_MMA)) {
                         ok = false;
@@ -380,7 +428,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     }
                     tc_fence_after();
                 }
-                for (int kb = 0; kb < nkb; ++kb) {
+                for (int kb = 0; kb < tnkb; ++kb) {
                     const int kin = Cfg::CHUNK > 0 ? kb % Cfg::CHUNK : kb;  // K block within the chunk
                     if (Cfg::CHUNK > 0 && kin == 0) {
                         // a fresh accumulator for each chunk, folded by the epilogue
@@ -429,7 +477,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                         }
                     }
                     if (!ok) break;
-                    if (Cfg::CHUNK > 0 && (kin == Cfg::CHUNK - 1 || kb == nkb - 1)) {
+                    if (Cfg::CHUNK > 0 && (kin == Cfg::CHUNK - 1 || kb == tnkb - 1)) {
                         mma_commit(&accf_bar[acc]);
                         if (++acc == Cfg::ACC_BUFS) {
                             acc = 0;
@@ -469,13 +517,14 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         uint32_t acc_phase = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            int tm, tn;
-            coords(t, tm, tn);
+            const TileInfo ti = tile_info(t);
+            const int tm = ti.tm;
             const int row = tm * Cfg::BM + q * 32 + lane;
-            const int n0 = tn * Cfg::BN + col0;
-            float* crow = p.C + (size_t)row * p.ldc;
-            const bool row_ok = row < p.M;
-            const bool vec = ((p.ldc & 3) == 0) && ((((uintptr_t)p.C) & 15u) == 0);
+            const int n0 = ti.tn * Cfg::BN + col0;
+            const int tN = ti.N;
+            float* crow = ti.C + (size_t)row * ti.ldc;
+            const bool row_ok = row < ti.M;
+            const bool vec = ((ti.ldc & 3) == 0) && ((((uintptr_t)ti.C) & 15u) == 0);
             if (Cfg::CHUNK > 0) {
                 constexpr int NCOL = Cfg::BN / (Cfg::EPI_WARPS / 4);
                 // running FP32 sums as pairs: acc2[j] holds columns 2j, 2j + 1
@@ -483,7 +532,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < NCOL / 2; ++j) acc2[j] = 0ull;
                 const int ksa = (p.K + 127) / 128, nsb = (p.N + 127) / 128;
-                const int nchunks = (nkb + Cfg::CHUNK - 1) / Cfg::CHUNK;
+                const int nchunks = (ti.nkb + Cfg::CHUNK - 1) / Cfg::CHUNK;
                 // FP8 chunk factors sA * sB, 32 chunks per window: lane j holds the factor
                 // of chunk 32 w + j of the current window (cur) and of the next one (nxt),
                 // loaded a whole window before use, so that the global-load latency never
@@ -557,7 +606,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                         const int n = n0 + j;
                         const float v4[4] = {f2_lo(acc2[j / 2]), f2_hi(acc2[j / 2]),
                                              f2_lo(acc2[j / 2 + 1]), f2_hi(acc2[j / 2 + 1])};
-                        if (vec && n + 3 < p.N) {
+                        if (vec && n + 3 < tN) {
                             float4 o = make_float4(v4[0], v4[1], v4[2], v4[3]);
                             if (p.beta) {
                                 const float4 c = *reinterpret_cast<const float4*>(crow + n);
@@ -566,7 +615,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                             *reinterpret_cast<float4*>(crow + n) = o;
                         } else {
                             for (int u = 0; u < 4; ++u)
-                                if (n + u < p.N) crow[n + u] = p.beta ? crow[n + u] + v4[u] : v4[u];
+                                if (n + u < tN) crow[n + u] = p.beta ? crow[n + u] + v4[u] : v4[u];
                         }
                     }
                 }
@@ -595,7 +644,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
 #pragma unroll
                         for (int j = 0; j < 32; j += 4) {
                             const int n = nb + j;
-                            if (vec && n + 3 < p.N) {
+                            if (vec && n + 3 < tN) {
                                 float4 o = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
                                                        __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
                                 if (p.beta) {
@@ -605,7 +654,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                                 *reinterpret_cast<float4*>(crow + n) = o;
                             } else {
                                 for (int u = 0; u < 4; ++u)
-                                    if (n + u < p.N) {
+                                    if (n + u < tN) {
                                         const float v = __uint_as_float(r[j + u]);
                                         crow[n + u] = p.beta ? crow[n + u] + v : v;
                                     }
@@ -847,6 +896,183 @@ pgk_status tc_gemm_launch(const pgk_case& c, int M, int N, int K, pgk_dtype dtyp
     const int grid = (int)std::min<long long>(tiles, m.sm_count);
     cudaError_t e = t[i].launch(ma, mb, ma2, mb2, p, grid, stream);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
+    return PGK_OK;
+}
+
+// ------------------------------------------------------- grouped launches
+template <class Cfg>
+static cudaError_t launch_tc_grouped(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& a2,
+                                     const CUtensorMap& b2, const TcParams& p, int grid,
+                                     cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_tc_gemm<Cfg, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<Cfg, true><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a, b, a2, b2, p);
+    return cudaGetLastError();
+}
+
+struct TcGroupedVariant {
+    pgk_dtype dtype;
+    int BN, stages;
+    tc_launch_fn launch;
+};
+
+// 128-wide tiles only: a group of uneven problems wastes less on ragged edges
+static const TcGroupedVariant* tcg_table(int* n) {
+    static const TcGroupedVariant t[] = {
+        {PGK_BF16, 128, 6, launch_tc_grouped<TcCfg<MODE_BF16, 128, 6>>},
+        {PGK_SPLIT_BF16, 128, 3, launch_tc_grouped<TcCfg<MODE_SPLIT, 128, 3>>},
+        {PGK_SPLIT_BF16, 128, 6, launch_tc_grouped<TcCfg<MODE_SPLIT3, 128, 6>>},
+    };
+    *n = (int)(sizeof(t) / sizeof(t[0]));
+    return t;
+}
+
+int tc_grouped_variants(pgk_dtype dtype, pgk_params* out, int cap) {
+    int n, k = 0;
+    const TcGroupedVariant* t = tcg_table(&n);
+    for (int i = 0; i < n; ++i)
+        if (t[i].dtype == dtype) {
+            if (out && k < cap) out[k] = pgk_params{128, t[i].BN, t[i].stages, 0, 64};
+            ++k;
+        }
+    return k;
+}
+
+pgk_status launch_cvt_grouped(int mode, int transpose, const GCvt* probs, const int* prefix, int G,
+                              int total, uint16_t* d0, uint16_t* d1, long long ldd, cudaStream_t st);
+
+// G problems in the BF16 or split form: one grouped conversion of all A operands,
+// one of all B operands (transposed), both into packed K-major workspaces, then
+// one persistent tensor-core launch over the tiles of every problem, problems in
+// decreasing K order.  Problem g's operands start at a multiple of 128 rows and
+// are zero from K_g to the next multiple of 64, so every tile computes exactly
+// what a single launch on that problem computes.
+pgk_status tc_gemm_grouped(int G, const pgk_problem* pr, pgk_dtype dtype, const pgk_params* prog,
+                           int beta, cudaStream_t s) {
+    pgk_params pp = {128, 128, dtype == PGK_BF16 ? 6 : 3, 0, 64};
+    if (prog) pp = *prog;
+    if (pp.B0 != 128 || (pp.tile != 0 && pp.tile != 64)) {
+        set_error("grouped tensor-core tiles are 128 x B1 x 64 (B0=%d tile=%d)", pp.B0, pp.tile);
+        return PGK_ERR_UNSUPPORTED;
+    }
+    int nv;
+    const TcGroupedVariant* tv = tcg_table(&nv);
+    const TcGroupedVariant* v = nullptr;
+    for (int i = 0; i < nv; ++i)
+        if (tv[i].dtype == dtype && tv[i].BN == pp.B1 && tv[i].stages == pp.s) v = &tv[i];
+    if (!v) {
+        set_error("no grouped tensor-core variant with B1=%d stages=%d for this form", pp.B1, pp.s);
+        return PGK_ERR_UNSUPPORTED;
+    }
+    pgk_status st = get_encoder();
+    if (st != PGK_OK) return st;
+    pgk_machine m;
+    if ((st = current_machine(&m, NULL)) != PGK_OK) return st;
+
+    std::vector<int> order(G);
+    for (int i = 0; i < G; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pr[a].K > pr[b].K; });
+    int kmax = 0;
+    long long rowsA = 0, rowsB = 0, tiles = 0, itemsA = 0, itemsB = 0;
+    for (int i = 0; i < G; ++i) {
+        const pgk_problem& q = pr[i];
+        kmax = std::max(kmax, q.K);
+        rowsA += (q.M + 127) / 128 * 128;
+        rowsB += (q.N + 127) / 128 * 128;
+        tiles += (long long)((q.M + 127) / 128) * ((q.N + v->BN - 1) / v->BN);
+        const long long kr = (q.K + 63) / 64;
+        itemsA += (long long)((q.M + 63) / 64) * kr;
+        itemsB += kr * ((q.N + 63) / 64);
+    }
+    const long long kst = (long long)(kmax + 63) / 64 * 64;   // row stride of the packed operands
+    if (rowsA > INT_MAX - 256 || rowsB > INT_MAX - 256 || tiles > INT_MAX || itemsA > INT_MAX ||
+        itemsB > INT_MAX) {
+        set_error("grouped tensor-core problem set too large for one launch");
+        return PGK_ERR_INVALID_ARG;
+    }
+    // host image of the tables: TcProb[G] | GCvt A[G] | GCvt B[G] | int4 tiles[T] |
+    // int prefixA[G+1] | int prefixB[G+1]
+    const size_t off_gA = (sizeof(TcProb) * G + 15) / 16 * 16;
+    const size_t off_gB = off_gA + (sizeof(GCvt) * G + 15) / 16 * 16;
+    const size_t off_t = off_gB + (sizeof(GCvt) * G + 15) / 16 * 16;
+    const size_t off_pA = off_t + sizeof(int4) * (size_t)tiles;
+    const size_t off_pB = off_pA + (sizeof(int) * (G + 1) + 15) / 16 * 16;
+    const size_t bytes = off_pB + sizeof(int) * (G + 1);
+    std::vector<unsigned char> img(bytes, 0);
+    TcProb* tp = reinterpret_cast<TcProb*>(img.data());
+    GCvt* ga = reinterpret_cast<GCvt*>(img.data() + off_gA);
+    GCvt* gb = reinterpret_cast<GCvt*>(img.data() + off_gB);
+    int4* tl = reinterpret_cast<int4*>(img.data() + off_t);
+    int* pa = reinterpret_cast<int*>(img.data() + off_pA);
+    int* pb = reinterpret_cast<int*>(img.data() + off_pB);
+    long long ra = 0, rb = 0, t = 0, ia = 0, ib = 0;
+    for (int j = 0; j < G; ++j) {
+        const pgk_problem& q = pr[order[j]];
+        const int kr = (q.K + 63) / 64 * 64;
+        tp[j] = TcProb{q.C, q.M, q.N, q.K, q.ldc, (int)ra, (int)rb};
+        const int va = ((uintptr_t)q.A % 16 == 0) && q.lda % 4 == 0;
+        const int vb = ((uintptr_t)q.B % 16 == 0) && q.ldb % 4 == 0;
+        ga[j] = GCvt{q.A, q.lda, q.M, q.K, kr, va, 0, ra};
+        gb[j] = GCvt{q.B, q.ldb, q.K, q.N, kr, vb, 0, rb};
+        pa[j] = (int)ia;
+        pb[j] = (int)ib;
+        ia += (long long)((q.M + 63) / 64) * (kr / 64);
+        ib += (long long)(kr / 64) * ((q.N + 63) / 64);
+        const int tm_n = (q.M + 127) / 128, tn_n = (q.N + v->BN - 1) / v->BN;
+        for (int tm = 0; tm < tm_n; ++tm)
+            for (int tn = 0; tn < tn_n; ++tn) tl[t++] = make_int4(j, tm, tn, 0);
+        ra += (q.M + 127) / 128 * 128;
+        rb += (q.N + 127) / 128 * 128;
+    }
+    pa[G] = (int)ia;
+    pb[G] = (int)ib;
+
+    unsigned char* dt = (unsigned char*)workspace(WS_TABLE, bytes, &st);
+    if (!dt) return st;
+    const bool split = dtype == PGK_SPLIT_BF16;
+    const size_t abytes = (size_t)rowsA * kst * 2, bbytes = (size_t)rowsB * kst * 2;
+    uint16_t* a0 = (uint16_t*)workspace(WS_A0, abytes, &st);
+    if (!a0) return st;
+    uint16_t* b0 = (uint16_t*)workspace(WS_B0, bbytes, &st);
+    if (!b0) return st;
+    uint16_t* a1 = nullptr;
+    uint16_t* b1 = nullptr;
+    if (split) {
+        if (!(a1 = (uint16_t*)workspace(WS_A1, abytes, &st))) return st;
+        if (!(b1 = (uint16_t*)workspace(WS_B1, bbytes, &st))) return st;
+    }
+    PGK_CUDA_TRY(cudaMemcpyAsync(dt, img.data(), bytes, cudaMemcpyHostToDevice, s), "table upload");
+    const int mode = split ? 1 : 0;
+    if ((st = launch_cvt_grouped(mode, 0, reinterpret_cast<const GCvt*>(dt + off_gA),
+                                 reinterpret_cast<const int*>(dt + off_pA), G, (int)itemsA, a0, a1, kst,
+                                 s)) != PGK_OK)
+        return st;
+    if ((st = launch_cvt_grouped(mode, 1, reinterpret_cast<const GCvt*>(dt + off_gB),
+                                 reinterpret_cast<const int*>(dt + off_pB), G, (int)itemsB, b0, b1, kst,
+                                 s)) != PGK_OK)
+        return st;
+    CUtensorMap ma, mb, ma2, mb2;
+    if ((st = make_map(&ma, a0, (int)rowsA, (int)kst, (int)kst, 2, 128)) != PGK_OK) return st;
+    if ((st = make_map(&mb, b0, (int)rowsB, (int)kst, (int)kst, 2, v->BN)) != PGK_OK) return st;
+    if (split) {
+        if ((st = make_map(&ma2, a1, (int)rowsA, (int)kst, (int)kst, 2, 128)) != PGK_OK) return st;
+        if ((st = make_map(&mb2, b1, (int)rowsB, (int)kst, (int)kst, 2, v->BN)) != PGK_OK) return st;
+    } else {
+        ma2 = ma;
+        mb2 = mb;
+    }
+    TcParams p;
+    memset(&p, 0, sizeof(p));
+    p.beta = beta ? 1 : 0;
+    p.err = device_error_word(&st);
+    if (!p.err) return st;
+    p.gtiles = reinterpret_cast<const int4*>(dt + off_t);
+    p.gprobs = reinterpret_cast<const TcProb*>(dt);
+    p.ntiles_g = (int)tiles;
+    const int grid = (int)std::min<long long>(tiles, m.sm_count);
+    cudaError_t e = v->launch(ma, mb, ma2, mb2, p, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped tensor-core GEMM launch");
     return PGK_OK;
 }
 

@@ -10,7 +10,8 @@ scale      FP32 at 4096^3, 8192^3, 8192 x 1024 x 4096, 16384 x 64 x 16384: full 
 grouped    512 FP32 GEMMs, M, N, K log-uniform in [32, 2048] (multiples of 16, seed 0),
            normal(0,1) operands: one grouped persistent launch (eager and CUDA-graph
            replay, tile variant from pgk_autotune_grouped) against 512 separate pgk_gemm
-           launches (eager and captured in one CUDA graph).
+           launches (eager and captured in one CUDA graph); and the same group in the
+           BF16 and split forms (grouped conversions + one tensor-core launch).
 mm         the paper's Table "mm" grid on GB300: int32, n = 2^10 and 2^11, (ub1, B0) x s.
 transpose  the paper's transposition grid at order 2^14 (GB/s).
 jacobi     the paper's 1D Jacobi grid (T = 4, length 2^15 + 2; and 2^27 + 2).
@@ -58,6 +59,16 @@ def _events_ms(fn, reps, stream):
         b.synchronize()
         ts.append(a.elapsed_time(b))
     return statistics.median(ts)
+
+
+def _oracle_rows(A, B, rows):
+    import oracle
+    return oracle.gemm(A, B, rows=rows)
+
+
+def _rel_frob(got, ref):
+    import oracle
+    return oracle.rel_frobenius(got.astype(np.float64), ref)
 
 
 def _rel_err_rows(Cd, A, B, rows):
@@ -159,7 +170,26 @@ def grouped(dev, stream):
     replay = lambda: g.replay()
     replay()
     t_sep_graph = _events_ms(replay, 10, stream)
+    # the tensor-core forms of the same group (three launches: A, B conversions, GEMM)
+    host_rows = []
+    for i, (M, N, K) in enumerate(dims[:64]):
+        A, B = inputs.gemm_operands(int(M), int(N), int(K), seed=1 + 2 * i, dist="normal")
+        rows = np.unique(np.linspace(0, int(M) - 1, 4).astype(np.int64))
+        host_rows.append((rows, _oracle_rows(A, B, rows)))
+    tc = {}
+    for name, dt, prog in (("bf16", pgk.BF16, pgk.params(128, 128, 6, 0, 64)),
+                           ("split", pgk.SPLIT_BF16, pgk.params(128, 128, 3, 0, 64)),
+                           ("split3", pgk.SPLIT_BF16, pgk.params(128, 128, 6, 0, 64))):
+        run = lambda: pgk.gemm_grouped(probs, dt, prog, stream=sh)
+        run()
+        ms = _events_ms(run, 10, stream)
+        torch.cuda.synchronize()
+        err = max(_rel_frob(trip[i][2][torch.from_numpy(r).to(dev)].cpu().numpy(), ref)
+                  for i, (r, ref) in enumerate(host_rows))
+        tc[name] = {"params": list(prog.as_tuple()), "ms": ms, "tflops": flops / ms / 1e9,
+                    "max_rel_err_first_64_problems": err}
     return {"config": "grouped 512 GEMMs", "flops": flops, "tile_variant": list(best.as_tuple()),
+            "tensor_core_forms": tc,
             "variant_sweep_ms": [(list(p.as_tuple()), t) for p, t in table],
             "grouped_ms": t_grouped, "grouped_graph_ms": t_grouped_graph,
             "separate_ms": t_sep, "separate_graph_ms": t_sep_graph,

@@ -84,3 +84,61 @@ def test_invalid_problem_rejected(dev):
     with pytest.raises(pgk.PgkError) as e:
         pgk.gemm_grouped(probs)
     assert e.value.status == 1
+
+
+TC_FORMS = [(pgk.BF16, pgk.params(128, 128, 6, 0, 64)),
+            (pgk.SPLIT_BF16, pgk.params(128, 128, 3, 0, 64)),
+            (pgk.SPLIT_BF16, pgk.params(128, 128, 6, 0, 64))]
+
+
+@pytest.mark.parametrize("dtype,prog", TC_FORMS)
+def test_tensor_core_group_equals_single_launches(dev, dtype, prog):
+    """The BF16 / split forms of a ragged group (sizes 1..300, odd K, unaligned
+    strides): every problem equals pgk_gemm on it with the same tile program, bit
+    for bit, for beta = 0 and 1 (packed operands at 128-row offsets, K zero-padded
+    to the 64-deep block: the same tile arithmetic as a single launch)."""
+    rng = np.random.default_rng(11)
+    dims = rng.integers(1, 300, size=(30, 3))
+    dims[0] = (1, 1, 1)
+    dims[1] = (129, 257, 65)
+    host, dt = make_group(dev, dims, 500)
+    # one problem with padded strides (lda > K, ldb > N, ldc > N)
+    M, N, K = 70, 90, 110
+    A, B = inputs.gemm_operands(M, N, K, seed=77, dist="normal")
+    Aw = torch.zeros(M, K + 5, device=dev)
+    Aw[:, :K] = torch.from_numpy(A)
+    Bw = torch.zeros(K, N + 3, device=dev)
+    Bw[:, :N] = torch.from_numpy(B)
+    Cw = torch.full((M, N + 7), float("nan"), device=dev)
+    host.append((A, B))
+    dt.append((Aw[:, :K], Bw[:, :N], Cw[:, :N]))
+    probs = pgk.make_problems(dt)
+    for beta in (0, 1):
+        if beta:
+            for _, _, Cd in dt:
+                Cd.copy_(torch.randn_like(Cd))
+        before = [Cd.clone() for _, _, Cd in dt]
+        pgk.gemm_grouped(probs, dtype, prog, beta=beta)
+        torch.cuda.synchronize()
+        for (Ad, Bd, Cd), C0 in zip(dt, before):
+            single = C0.clone()
+            pgk.gemm(Ad, Bd, single, dtype, prog, beta=beta)
+            torch.cuda.synchronize()
+            assert torch.equal(single, Cd), (dtype, prog.as_tuple(), beta, tuple(Ad.shape), Bd.shape[1])
+    assert torch.isnan(Cw[:, N:]).all()
+
+
+def test_config3_512_problems_split_form(dev):
+    """The 512-problem set in the split form: sampled rows of every problem within
+    the split tolerance of the FP64 oracle."""
+    dims = inputs.log_uniform_dims(512, 0, 32, 2048, 16)
+    host, dt = make_group(dev, dims, 1)
+    probs = pgk.make_problems(dt)
+    pgk.gemm_grouped(probs, pgk.SPLIT_BF16, None)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for (A, B), (_, _, Cd) in zip(host, dt):
+        rows = np.unique(np.linspace(0, A.shape[0] - 1, 4).astype(np.int64))
+        ref = oracle.gemm(A, B, rows=rows)
+        worst = max(worst, oracle.rel_frobenius(Cd.cpu().numpy()[rows].astype(np.float64), ref))
+    assert worst <= 2e-5, worst
