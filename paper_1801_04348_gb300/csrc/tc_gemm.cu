@@ -69,10 +69,13 @@ struct TcCfg {
     // chunk accumulators so the MMA can run three chunks ahead of the epilogue
     static constexpr int ACC_BUFS = (MODE == MODE_FP8 && BN == 128) ? 4 : 2;
     static constexpr int TMEM_COLS = ACC_BUFS * BN;
-    static constexpr int SMEM_RAW = STAGES * STAGE_BYTES + 1024;
+    // epilogue staging: one 32 x 33 FP32 block per epilogue warp after the stage ring
+    static constexpr int XPOSE_BYTES = EPI_WARPS * 32 * 33 * 4;
+    static constexpr int SMEM_RAW = STAGES * STAGE_BYTES + XPOSE_BYTES + 1024;
     // at least 116 KB so that one CTA owns the SM (and its tensor memory)
     static constexpr int SMEM = SMEM_RAW > 118784 ? SMEM_RAW : 118784;
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation is a power of two");
+    static_assert(SMEM <= 232448 - 512, "stage ring, staging blocks and barriers fit the opt-in shared memory");
     static_assert(CHUNK == 0 || BN / (EPI_WARPS / 4) <= 128, "promoted columns per warp");
 };
 
@@ -511,6 +514,28 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         // -------------------------------------------------------- epilogue
         const int e = warp - 2;
         const int q = warp & 3;                       // TMEM lane quarter of this warp
+        // a thread holds 32 consecutive columns of its own row after tcgen05.ld; the
+        // block goes through this warp's shared staging (pitch 33: conflict-free both
+        // ways) so that every store instruction covers 32 consecutive columns of a row
+        float* xp = reinterpret_cast<float*>(tiles + (size_t)Cfg::STAGES * Cfg::STAGE_BYTES) +
+                    e * (32 * 33);
+        auto store_block = [&](const float (&v)[32], int row0, int cb, int M, int N, float* C,
+                               int ldc) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) xp[lane * 33 + j] = v[j];
+            __syncwarp();
+            const int col = cb + lane;
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = row0 + rr;
+                if (row < M && col < N) {
+                    float* cp = C + (size_t)row * ldc + col;
+                    const float x = xp[rr * 33 + lane];
+                    *cp = p.beta ? *cp + x : x;
+                }
+            }
+            __syncwarp();
+        };
         const int ncol = Cfg::BN / (Cfg::EPI_WARPS / 4);  // columns handled by this warp
         const int col0 = (e >> 2) * ncol;
         int acc = 0;
@@ -519,12 +544,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const TileInfo ti = tile_info(t);
             const int tm = ti.tm;
-            const int row = tm * Cfg::BM + q * 32 + lane;
+            const int row0 = tm * Cfg::BM + q * 32;   // first of the 32 rows of this warp
             const int n0 = ti.tn * Cfg::BN + col0;
             const int tN = ti.N;
-            float* crow = ti.C + (size_t)row * ti.ldc;
-            const bool row_ok = row < ti.M;
-            const bool vec = ((ti.ldc & 3) == 0) && ((((uintptr_t)ti.C) & 15u) == 0);
             if (Cfg::CHUNK > 0) {
                 constexpr int NCOL = Cfg::BN / (Cfg::EPI_WARPS / 4);
                 // running FP32 sums as pairs: acc2[j] holds columns 2j, 2j + 1
@@ -532,7 +554,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < NCOL / 2; ++j) acc2[j] = 0ull;
                 const int ksa = (p.K + 127) / 128, nsb = (p.N + 127) / 128;
-                const int nchunks = (ti.nkb + Cfg::CHUNK - 1) / Cfg::CHUNK;
+                constexpr int CH = Cfg::CHUNK > 0 ? Cfg::CHUNK : 1;   // (this branch has CHUNK > 0)
+                const int nchunks = (ti.nkb + CH - 1) / CH;
                 // FP8 chunk factors sA * sB, 32 chunks per window: lane j holds the factor
                 // of chunk 32 w + j of the current window (cur) and of the next one (nxt),
                 // loaded a whole window before use, so that the global-load latency never
@@ -600,24 +623,15 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     }
                 }
                 if (!ok) break;
-                if (row_ok) {
 #pragma unroll
-                    for (int j = 0; j < NCOL; j += 4) {
-                        const int n = n0 + j;
-                        const float v4[4] = {f2_lo(acc2[j / 2]), f2_hi(acc2[j / 2]),
-                                             f2_lo(acc2[j / 2 + 1]), f2_hi(acc2[j / 2 + 1])};
-                        if (vec && n + 3 < tN) {
-                            float4 o = make_float4(v4[0], v4[1], v4[2], v4[3]);
-                            if (p.beta) {
-                                const float4 c = *reinterpret_cast<const float4*>(crow + n);
-                                o.x += c.x; o.y += c.y; o.z += c.z; o.w += c.w;
-                            }
-                            *reinterpret_cast<float4*>(crow + n) = o;
-                        } else {
-                            for (int u = 0; u < 4; ++u)
-                                if (n + u < tN) crow[n + u] = p.beta ? crow[n + u] + v4[u] : v4[u];
-                        }
+                for (int g = 0; g < NCOL / 32; ++g) {
+                    float v[32];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        v[2 * i] = f2_lo(acc2[g * 16 + i]);
+                        v[2 * i + 1] = f2_hi(acc2[g * 16 + i]);
                     }
+                    store_block(v, row0, n0 + g * 32, ti.M, tN, ti.C, ti.ldc);
                 }
             } else {
                 int w = 1;
@@ -639,28 +653,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                                   (uint32_t)(acc * Cfg::BN + col0 + c * 32),
                               r);
                     tmem_ld_wait();
-                    if (row_ok) {
-                        const int nb = n0 + c * 32;
+                    float v[32];
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4) {
-                            const int n = nb + j;
-                            if (vec && n + 3 < tN) {
-                                float4 o = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                                       __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-                                if (p.beta) {
-                                    const float4 cc = *reinterpret_cast<const float4*>(crow + n);
-                                    o.x += cc.x; o.y += cc.y; o.z += cc.z; o.w += cc.w;
-                                }
-                                *reinterpret_cast<float4*>(crow + n) = o;
-                            } else {
-                                for (int u = 0; u < 4; ++u)
-                                    if (n + u < tN) {
-                                        const float v = __uint_as_float(r[j + u]);
-                                        crow[n + u] = p.beta ? crow[n + u] + v : v;
-                                    }
-                            }
-                        }
-                    }
+                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                    store_block(v, row0, n0 + c * 32, ti.M, tN, ti.C, ti.ldc);
                 }
                 tc_fence_before();
                 __syncwarp();
