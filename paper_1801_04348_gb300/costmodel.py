@@ -258,7 +258,7 @@ def main():
     import torch
     ap = argparse.ArgumentParser(description="learned case selection: collect, train, evaluate")
     ap.add_argument("--out", required=True, help="output directory")
-    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "split"])
     ap.add_argument("--eval-shapes", type=int, default=1000)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--epochs", type=int, default=200)
