@@ -215,10 +215,11 @@ PGK_API pgk_status pgk_gemm(int M, int N, int K, pgk_dtype dtype, const float* A
  * The library copies A and B into one of two device buffer sets that it owns,
  * on a stream of its own, then runs the GEMM on `stream`; consecutive calls
  * alternate the sets, so the input copies of one call run while the GEMM of the
- * previous call computes.  The GEMM runs in two row panels (the first ending on a
- * multiple of 128 rows; the tensor-core forms convert B once) into a device
- * buffer; the first panel's C is copied back on a second library stream while
- * the second panel computes, and `stream` waits for both copies.  Pinned
+ * previous call computes.  The GEMM runs in row panels (boundaries at multiples
+ * of 128 rows, panels of whole rounds of tiles for the SM count, at most 8; the
+ * tensor-core forms convert B once) into a device buffer; each panel's C is
+ * copied back on a second library stream while the next panel computes, and
+ * `stream` waits for the copies.  Pinned
  * buffers (cudaHostAlloc / cudaMallocHost / cudaHostRegister) copy at the host
  * link's full rate; pageable memory works but the driver stages it.
  * Ordering: the input copies are not ordered after work enqueued on `stream`

@@ -1,14 +1,17 @@
 // GEMM on host buffers.  The inputs are copied into one of two library-owned
 // device buffer sets on a library stream, so that the copies of call i + 1 run
-// while call i computes.  The GEMM runs on the caller's stream in two row panels
-// (split at a multiple of 128 rows, so that every tile and FP8 scale block is the
-// one of the whole matrix; the tensor-core forms convert B once): the first
-// panel's C is copied back to host memory on a second library stream while the
-// second panel computes, and the caller's stream waits for both copies.  C stays
-// in device memory until copied: stores from the GEMM epilogue straight into
-// host memory stall the tensor-core pipeline on the host link.
+// while call i computes.  The GEMM runs on the caller's stream in row panels
+// (boundaries at multiples of 128 rows, so that every tile and FP8 scale block
+// is the one of the whole matrix; the tensor-core forms convert B once).  Each
+// panel's C is copied back on a second library stream while the next panel
+// computes, and the caller's stream waits for the copies; only the last panel's
+// copy is not hidden.  Panels hold whole rounds of tiles (a multiple of the SM
+// count), so the split costs no extra rounds of the persistent grid and the last
+// panel is small.  C stays in device memory until copied: stores from the GEMM
+// epilogue straight into host memory stall the tensor-core pipeline on the host link.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "pgk_internal.cuh"
@@ -30,8 +33,8 @@ struct HostIO {
     int device = -1;
     cudaStream_t s_in = nullptr;           // input copies
     cudaStream_t s_out = nullptr;          // copy-back of the first panel
-    cudaEvent_t panel_done = nullptr;      // first panel computed
-    cudaEvent_t out_done = nullptr;        // first panel copied back
+    cudaEvent_t panel_done[8] = {};        // panel computed
+    cudaEvent_t out_done = nullptr;        // every panel copied back
     HostSet set[2];
     int next = 0;
 };
@@ -67,7 +70,8 @@ pgk_status state_for_device(int dev, HostIO** out) {
     if (h.device < 0) {
         PGK_CUDA_TRY(cudaStreamCreateWithFlags(&h.s_in, cudaStreamNonBlocking), "stream create");
         PGK_CUDA_TRY(cudaStreamCreateWithFlags(&h.s_out, cudaStreamNonBlocking), "stream create");
-        PGK_CUDA_TRY(cudaEventCreateWithFlags(&h.panel_done, cudaEventDisableTiming), "event create");
+        for (auto& e : h.panel_done)
+            PGK_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create");
         PGK_CUDA_TRY(cudaEventCreateWithFlags(&h.out_done, cudaEventDisableTiming), "event create");
         for (auto& s : h.set) {
             PGK_CUDA_TRY(cudaEventCreateWithFlags(&s.in_done, cudaEventDisableTiming), "event create");
@@ -87,6 +91,23 @@ cudaMemoryType memory_type(const void* p) {
         return cudaMemoryTypeUnregistered;
     }
     return a.type;
+}
+
+// Row panels in 128-row tile rows: the smallest panel of at least 1/8 of the tile
+// rows whose tile count (panel rows x column tiles of width bn) is a multiple of
+// the SM count, repeated, the remainder last; else two halves.  Returns the
+// number of panels (<= 8) and their first rows in starts[0..n] (starts[n] = M).
+int plan_panels(int M, int N, int bn, int sms, int* starts) {
+    const int T = (M + 127) / 128, tn = (N + bn - 1) / bn;
+    int r = 0;
+    if (T >= 2 && sms > 0)
+        for (int c = std::max(1, (T + 7) / 8); c <= T / 2 && !r; ++c)
+            if (((long long)c * tn) % sms == 0) r = c;
+    if (!r) r = T >= 2 ? (T + 1) / 2 : T;
+    int n = 0;
+    for (int t = 0; t < T; t += r) starts[n++] = t * 128;
+    starts[n] = M;
+    return n;
 }
 
 }  // namespace
@@ -111,7 +132,7 @@ void hostio_release() {
         (void)cudaStreamSynchronize(h.s_out);
         cudaStreamDestroy(h.s_in);
         cudaStreamDestroy(h.s_out);
-        cudaEventDestroy(h.panel_done);
+        for (auto& e : h.panel_done) cudaEventDestroy(e);
         cudaEventDestroy(h.out_done);
         h = HostIO();
     }
@@ -170,29 +191,29 @@ pgk_status pgk_gemm_host(int M, int N, int K, pgk_dtype dtype, const float* A, i
     PGK_CUDA_TRY(cudaEventRecord(set.in_done, h->s_in), "event record");
     PGK_CUDA_TRY(cudaStreamWaitEvent(st, set.in_done, 0), "stream wait");
 
-    // two row panels, the first ending on a multiple of 128 rows
-    const int m0 = M >= 256 ? (M / 2 + 127) / 128 * 128 : M;
-    s = gemm_device(m0, N, K, dtype, set.A, K, set.B, N, set.C, N, beta, prog, st, false);
-    if (s == PGK_OK && m0 < M) {
-        cudaError_t e = cudaEventRecord(h->panel_done, st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->panel_done, 0);
+    // row panels; the copy-back of panel i runs while panel i + 1 computes
+    int sms = 0;
+    PGK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const bool tc = dtype == PGK_BF16 || dtype == PGK_SPLIT_BF16 || dtype == PGK_FP8_E4M3;
+    const int bn = tc ? (prog ? prog->B1 : 256) : (prog ? std::max(1, prog->B1 * prog->s) : 128);
+    int starts[9];
+    const int np = plan_panels(M, N, bn, sms, starts);
+    for (int i = 0; i < np && s == PGK_OK; ++i) {
+        const int r0 = starts[i], rows = starts[i + 1] - r0;
+        s = gemm_device(rows, N, K, dtype, set.A + (size_t)r0 * K, K, set.B, N, set.C + (size_t)r0 * N, N,
+                        beta, prog, st, i > 0);
+        if (s != PGK_OK) break;
+        cudaError_t e = cudaEventRecord(h->panel_done[i], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->panel_done[i], 0);
         if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(C, ldc * fs, set.C, N * fs, N * fs, m0, cudaMemcpyDeviceToHost, h->s_out);
-        if (e == cudaSuccess) e = cudaEventRecord(h->out_done, h->s_out);
-        if (e != cudaSuccess) s = cuda_fail(e, "copy-back of the first panel");
-        if (s == PGK_OK)
-            s = gemm_device(M - m0, N, K, dtype, set.A + (size_t)m0 * K, K, set.B, N,
-                            set.C + (size_t)m0 * N, N, beta, prog, st, true);
-        if (s == PGK_OK) {
-            e = cudaMemcpy2DAsync(C + (size_t)m0 * ldc, ldc * fs, set.C + (size_t)m0 * N, N * fs, N * fs,
-                                  M - m0, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->out_done, 0);
-            if (e != cudaSuccess) s = cuda_fail(e, "copy-back of the second panel");
-        }
-    } else if (s == PGK_OK) {
-        const cudaError_t e = cudaMemcpy2DAsync(C, ldc * fs, set.C, N * fs, N * fs, M,
-                                                cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) s = cuda_fail(e, "copy of C");
+            e = cudaMemcpy2DAsync(C + (size_t)r0 * ldc, ldc * fs, set.C + (size_t)r0 * N, N * fs, N * fs,
+                                  rows, cudaMemcpyDeviceToHost, h->s_out);
+        if (e != cudaSuccess) s = cuda_fail(e, "copy-back of a panel");
+    }
+    {
+        cudaError_t e = cudaEventRecord(h->out_done, h->s_out);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->out_done, 0);
+        if (e != cudaSuccess && s == PGK_OK) s = cuda_fail(e, "copy-back ordering");
     }
     // the set is free again once the stream passes this point, also after a failure
     PGK_CUDA_TRY(cudaEventRecord(set.comp_done, st), "event record");
