@@ -263,7 +263,10 @@ PGK_API pgk_status pgk_gemm_case(const pgk_case* c, int M, int N, int K, const f
  * decreasing K order.  Each C_g equals, bit for bit, pgk_gemm on that problem
  * with the same tile program.  `prog` = (128, 128, stages, 0, 64): stages 6
  * for BF16, 3 (split) or 6 (split in three passes); NULL = the first.
- * use_graph does not apply.  No alignment condition on the problems.
+ * use_graph does not apply.  No alignment condition on the problems.  The packed
+ * workspaces hold every problem at the row stride of the largest K: about
+ * (sum of M_g and of N_g, each rounded up to 128) x max K x 2 bytes per operand
+ * plane (two planes each for split); a failed allocation returns NO_MEMORY.
  * Errors: INVALID_ARG (G < 1, a bad problem, a set too large for one launch),
  * UNSUPPORTED (FP8 / no such variant), CUDA, NO_MEMORY. */
 PGK_API pgk_status pgk_gemm_grouped(int G, const pgk_problem* problems, pgk_dtype dtype,
