@@ -256,19 +256,21 @@ PGK_API pgk_status pgk_gemm_case(const pgk_case* c, int M, int N, int K, const f
  * (NULL = tuned/default).  use_graph = 1 captures the counter reset and the
  * launch in a CUDA graph, cached per problem set and replayed on later calls
  * with the same problems.
- * PGK_BF16 / PGK_SPLIT_BF16: three launches on `stream`: one converts every A_g,
- * one every B_g (transposed), into library workspaces packed problem after
- * problem (each at a multiple of 128 rows, K zero-padded to a multiple of 64),
- * and one persistent tensor-core launch runs the tiles of all problems, in
- * decreasing K order.  Each C_g equals, bit for bit, pgk_gemm on that problem
- * with the same tile program.  `prog` = (128, 128, stages, 0, 64): stages 6
- * for BF16, 3 (split) or 6 (split in three passes); NULL = the first.
+ * PGK_BF16 / PGK_SPLIT_BF16 / PGK_FP8_E4M3: three launches on `stream`: one
+ * converts (FP8: quantises, 128 x 128 tile scales) every A_g, one every B_g
+ * (transposed), into library workspaces packed problem after problem (each at a
+ * multiple of 128 rows, K zero-padded to the K block, 64 or 128 for FP8), and one
+ * persistent tensor-core launch runs the tiles of all problems, in decreasing K
+ * order.  Each C_g equals, bit for bit, pgk_gemm on that problem with the same
+ * tile program.  `prog` = (128, 128, stages, 0, K block): stages 6 for BF16 and
+ * FP8, 3 (split) or 6 (split in three passes); NULL = the first.
  * use_graph does not apply.  No alignment condition on the problems.  The packed
  * workspaces hold every problem at the row stride of the largest K: about
  * (sum of M_g and of N_g, each rounded up to 128) x max K x 2 bytes per operand
- * plane (two planes each for split); a failed allocation returns NO_MEMORY.
+ * plane (two planes each for split, 1 byte per entry for FP8); a failed
+ * allocation returns NO_MEMORY.
  * Errors: INVALID_ARG (G < 1, a bad problem, a set too large for one launch),
- * UNSUPPORTED (FP8 / no such variant), CUDA, NO_MEMORY. */
+ * UNSUPPORTED (no such variant), CUDA, NO_MEMORY. */
 PGK_API pgk_status pgk_gemm_grouped(int G, const pgk_problem* problems, pgk_dtype dtype,
                             const pgk_params* prog, int use_graph, int beta, void* stream);
 

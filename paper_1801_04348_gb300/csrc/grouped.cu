@@ -230,10 +230,10 @@ extern "C" pgk_status pgk_gemm_grouped(int G, const pgk_problem* problems, pgk_d
                                        void* stream) {
     pgk_status st = check_problems(G, problems);
     if (st != PGK_OK) return st;
-    if (dtype == PGK_BF16 || dtype == PGK_SPLIT_BF16)
+    if (dtype == PGK_BF16 || dtype == PGK_SPLIT_BF16 || dtype == PGK_FP8_E4M3)
         return tc_gemm_grouped(G, problems, dtype, prog, beta, (cudaStream_t)stream);
     if (dtype != PGK_F32) {
-        set_error("the grouped GEMM runs the FP32 SIMT family and the BF16 / split-BF16 forms");
+        set_error("the grouped GEMM runs the FP32 SIMT family and the tensor-core forms");
         return PGK_ERR_UNSUPPORTED;
     }
     pgk_params p;

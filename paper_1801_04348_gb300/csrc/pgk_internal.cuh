@@ -104,6 +104,18 @@ struct GCvt {
 pgk_status tc_gemm_grouped(int G, const pgk_problem* pr, pgk_dtype dtype, const pgk_params* prog,
                            int beta, cudaStream_t s);
 int tc_grouped_variants(pgk_dtype dtype, pgk_params* out, int cap);
+// One problem of a grouped FP8 quantisation (k_quant_fp8_grouped in prep.cu).
+struct GQuant {
+    const float* src;
+    int lds, rows, cols;
+    int width;          // padded K (a multiple of 128)
+    int vec;
+    int scale_off;      // A: first scale row (128-row block); B: first scale column
+    long long dst_row;  // first destination row in the packed code array
+};
+pgk_status launch_quant_fp8_grouped(int transpose, const GQuant* probs, const int* prefix, int G,
+                                    int total, uint8_t* dst, long long ldd, float* scales,
+                                    int ld_scales, cudaStream_t st);
 // mode 0: BF16, mode 1: hi/lo split.  total = prefix[G] tile items.
 pgk_status launch_cvt_grouped(int mode, int transpose, const GCvt* probs, const int* prefix, int G,
                               int total, uint16_t* d0, uint16_t* d1, long long ldd, cudaStream_t st);

@@ -172,17 +172,29 @@ __device__ __forceinline__ void store_codes(uint8_t* __restrict__ dst, size_t of
 static constexpr int QUANT_THREADS = 512;
 static constexpr int QUANT_PITCH = 129;
 
+// Problem of a grouped work item: the largest g with prefix[g] <= item.
+__device__ __forceinline__ int grouped_item_problem(const int* __restrict__ prefix, int G, int item) {
+    int lo = 0, hi = G - 1;   // largest g with prefix[g] <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One 128 x 128 tile at (r0, c0) of src (rows x cols, zero outside): its scale goes
+// to *scale_out, its codes to dst, in the source layout for columns below wbound
+// (rows mode) or transposed for source rows below wbound (the K extent; entries
+// between the source size and wbound are the codes of zeros).  Called by every
+// thread of a QUANT_THREADS block; red and tile are the block's shared buffers.
 template <bool TRANS>
-__global__ void __launch_bounds__(QUANT_THREADS) k_quant_fp8(int rows, int cols,
-                                                             const float* __restrict__ src, int lds,
-                                                             uint8_t* __restrict__ dst, int ldd,
-                                                             float* __restrict__ scales, int ld_scales,
-                                                             int vec_in, int vec_out) {
+__device__ __forceinline__ void quant_tile(const float* __restrict__ src, int lds, int rows, int cols,
+                                           int wbound, int r0, int c0, uint8_t* __restrict__ dst,
+                                           int ldd, float* scale_out, int vec_in, int vec_out,
+                                           float* red, uint8_t* tile) {
     constexpr int WARPS = QUANT_THREADS / 32;          // 16
     constexpr int NV = 128 * 128 / 4 / QUANT_THREADS;  // float4 per thread: 8
-    __shared__ float red[WARPS];
-    __shared__ uint8_t tile[TRANS ? 128 * QUANT_PITCH : 1];
-    const int r0 = blockIdx.y * 128, c0 = blockIdx.x * 128;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 v[NV];
 #pragma unroll
@@ -201,7 +213,7 @@ __global__ void __launch_bounds__(QUANT_THREADS) k_quant_fp8(int rows, int cols,
 #pragma unroll
     for (int w = 1; w < WARPS; ++w) amax = fmaxf(amax, red[w]);
     const float scale = amax == 0.f ? 1.f : __fdiv_rn(amax, 448.f);
-    if (threadIdx.x == 0) scales[(size_t)blockIdx.y * ld_scales + blockIdx.x] = scale;
+    if (threadIdx.x == 0) *scale_out = scale;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
         const int rr = i * WARPS + warp, cc = lane * 4;   // position in the tile
@@ -211,7 +223,7 @@ __global__ void __launch_bounds__(QUANT_THREADS) k_quant_fp8(int rows, int cols,
 #pragma unroll
             for (int k = 0; k < 4; ++k) tile[rr * QUANT_PITCH + cc + k] = (uint8_t)(w >> (8 * k));
         } else if (r0 + rr < rows) {
-            store_codes(dst, (size_t)(r0 + rr) * ldd + c0 + cc, w, min(4, cols - c0 - cc), vec_out);
+            store_codes(dst, (size_t)(r0 + rr) * ldd + c0 + cc, w, min(4, wbound - c0 - cc), vec_out);
         }
     }
     if (TRANS) {
@@ -226,9 +238,53 @@ __global__ void __launch_bounds__(QUANT_THREADS) k_quant_fp8(int rows, int cols,
             const uint32_t w = (uint32_t)col[0] | ((uint32_t)col[QUANT_PITCH] << 8) |
                                ((uint32_t)col[2 * QUANT_PITCH] << 16) |
                                ((uint32_t)col[3 * QUANT_PITCH] << 24);
-            store_codes(dst, (size_t)(c0 + j) * ldd + r0 + 4 * lane, w, min(4, rows - r0 - 4 * lane),
+            store_codes(dst, (size_t)(c0 + j) * ldd + r0 + 4 * lane, w, min(4, wbound - r0 - 4 * lane),
                         vec_out);
         }
+        __syncthreads();   // the shared tile may be reused by the block's next tile
+    }
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(QUANT_THREADS) k_quant_fp8(int rows, int cols,
+                                                             const float* __restrict__ src, int lds,
+                                                             uint8_t* __restrict__ dst, int ldd,
+                                                             float* __restrict__ scales, int ld_scales,
+                                                             int vec_in, int vec_out) {
+    __shared__ float red[QUANT_THREADS / 32];
+    __shared__ uint8_t tile[TRANS ? 128 * QUANT_PITCH : 1];
+    quant_tile<TRANS>(src, lds, rows, cols, TRANS ? rows : cols, blockIdx.y * 128, blockIdx.x * 128,
+                      dst, ldd, scales + (size_t)blockIdx.y * ld_scales + blockIdx.x, vec_in, vec_out,
+                      red, tile);
+}
+
+// Grouped quantisation: 128 x 128 tile items over every problem (numbered problem
+// after problem, prefix[g] = first item of problem g).  Problem g's codes go to
+// rows dst_row .. of the packed array (row stride ldd, zero codes up to `width`
+// along K), its tile scales to scales + scale_off with row stride ld_scales (A:
+// one row per 128-row block, B: one row per 128-deep K chunk).
+template <bool TRANS>
+__global__ void __launch_bounds__(QUANT_THREADS) k_quant_fp8_grouped(const GQuant* __restrict__ probs,
+                                                                     const int* __restrict__ prefix,
+                                                                     int G, int total,
+                                                                     uint8_t* __restrict__ dst,
+                                                                     long long ldd,
+                                                                     float* __restrict__ scales,
+                                                                     int ld_scales) {
+    __shared__ float red[QUANT_THREADS / 32];
+    __shared__ uint8_t tile[TRANS ? 128 * QUANT_PITCH : 1];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int g = grouped_item_problem(prefix, G, item);
+        const GQuant q = probs[g];
+        const int local = item - __ldg(prefix + g);
+        // rows mode: tiles over rows x width; transposed: over width x cols
+        const int tcols = TRANS ? (q.cols + 127) / 128 : q.width / 128;
+        const int ti = local / tcols, tj = local % tcols;
+        float* so = TRANS ? scales + (size_t)ti * ld_scales + q.scale_off + tj
+                          : scales + (size_t)(q.scale_off + ti) * ld_scales + tj;
+        quant_tile<TRANS>(q.src, q.lds, q.rows, q.cols, q.width, ti * 128, tj * 128,
+                          dst + (size_t)q.dst_row * ldd, (int)ldd, so, q.vec, 1, red, tile);
+        __syncthreads();   // red is reused by the next item
     }
 }
 
@@ -294,15 +350,6 @@ pgk_status launch_quant_fp8(int rows, int cols, const float* src, int lds, uint8
 // `width` entries hold source rows 0 .. width - 1 (zeros beyond `rows`).  The
 // work items are 64 x 64 tiles of the (padded) source, numbered problem after
 // problem; prefix[g] is the first item of problem g.
-__device__ __forceinline__ int grouped_item_problem(const int* __restrict__ prefix, int G, int item) {
-    int lo = 0, hi = G - 1;   // largest g with prefix[g] <= item
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(prefix + mid) <= item) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 template <int MODE, bool TRANS>
 __global__ void __launch_bounds__(256) k_cvt_grouped(const GCvt* __restrict__ probs,
@@ -403,6 +450,24 @@ pgk_status launch_cvt_grouped(int mode, int transpose, const GCvt* probs, const 
     else
         k_cvt_grouped<1, true><<<grid, 256, 0, st>>>(probs, prefix, G, total, d0, d1, ldd);
     PGK_CUDA_TRY(cudaGetLastError(), "grouped conversion launch");
+    return PGK_OK;
+}
+
+pgk_status launch_quant_fp8_grouped(int transpose, const GQuant* probs, const int* prefix, int G,
+                                    int total, uint8_t* dst, long long ldd, float* scales,
+                                    int ld_scales, cudaStream_t st) {
+    if (total < 1) return PGK_OK;
+    int dev = 0, sms = 0;
+    PGK_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    PGK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const int grid = std::min(total, std::max(sms, 1) * 2);
+    if (transpose)
+        k_quant_fp8_grouped<true><<<grid, QUANT_THREADS, 0, st>>>(probs, prefix, G, total, dst, ldd,
+                                                                 scales, ld_scales);
+    else
+        k_quant_fp8_grouped<false><<<grid, QUANT_THREADS, 0, st>>>(probs, prefix, G, total, dst, ldd,
+                                                                  scales, ld_scales);
+    PGK_CUDA_TRY(cudaGetLastError(), "grouped FP8 quantisation launch");
     return PGK_OK;
 }
 

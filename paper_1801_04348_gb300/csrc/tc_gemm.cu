@@ -277,7 +277,6 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
 
-    static_assert(!(GROUPED && Cfg::MODE == MODE_FP8), "grouped launches take BF16 or split operands");
     const int tiles_m = (p.M + Cfg::BM - 1) / Cfg::BM;
     const int tiles_n = (p.N + Cfg::BN - 1) / Cfg::BN;
     const int ntiles = GROUPED ? p.ntiles_g : tiles_m * tiles_n;
@@ -562,10 +561,13 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 // sits on the fold; each chunk takes its factor by a warp shuffle.  A warp
                 // whose columns all lie beyond N stores nothing; its scale index is
                 // clamped so that the loads stay inside the array.
-                const int nblk = min(n0 / 128, nsb - 1);
+                // scale blocks of this tile: its 128-row block of A and the 128-column block
+                // of B^T (both offset by the problem's first block in a grouped launch)
+                const int mblk = ti.rowA / 128 + tm;
+                const int nblk = ti.rowB / 128 + min(n0 / 128, (tN - 1) / 128);
                 auto chunk_scale = [&](int c) {
                     return c < nchunks
-                        ? __ldg(p.sA + (size_t)tm * ksa + c) * __ldg(p.sB + (size_t)c * nsb + nblk)
+                        ? __ldg(p.sA + (size_t)mblk * ksa + c) * __ldg(p.sB + (size_t)c * nsb + nblk)
                         : 0.f;
                 };
                 float sc_cur = 1.f, sc_nxt = 1.f;
@@ -919,6 +921,7 @@ static const TcGroupedVariant* tcg_table(int* n) {
         {PGK_BF16, 128, 6, launch_tc_grouped<TcCfg<MODE_BF16, 128, 6>>},
         {PGK_SPLIT_BF16, 128, 3, launch_tc_grouped<TcCfg<MODE_SPLIT, 128, 3>>},
         {PGK_SPLIT_BF16, 128, 6, launch_tc_grouped<TcCfg<MODE_SPLIT3, 128, 6>>},
+        {PGK_FP8_E4M3, 128, 6, launch_tc_grouped<TcCfg<MODE_FP8, 128, 6>>},
     };
     *n = (int)(sizeof(t) / sizeof(t[0]));
     return t;
@@ -929,7 +932,8 @@ int tc_grouped_variants(pgk_dtype dtype, pgk_params* out, int cap) {
     const TcGroupedVariant* t = tcg_table(&n);
     for (int i = 0; i < n; ++i)
         if (t[i].dtype == dtype) {
-            if (out && k < cap) out[k] = pgk_params{128, t[i].BN, t[i].stages, 0, 64};
+            if (out && k < cap)
+                out[k] = pgk_params{128, t[i].BN, t[i].stages, 0, dtype == PGK_FP8_E4M3 ? 128 : 64};
             ++k;
         }
     return k;
@@ -938,18 +942,26 @@ int tc_grouped_variants(pgk_dtype dtype, pgk_params* out, int cap) {
 pgk_status launch_cvt_grouped(int mode, int transpose, const GCvt* probs, const int* prefix, int G,
                               int total, uint16_t* d0, uint16_t* d1, long long ldd, cudaStream_t st);
 
-// G problems in the BF16 or split form: one grouped conversion of all A operands,
-// one of all B operands (transposed), both into packed K-major workspaces, then
-// one persistent tensor-core launch over the tiles of every problem, problems in
-// decreasing K order.  Problem g's operands start at a multiple of 128 rows and
-// are zero from K_g to the next multiple of 64, so every tile computes exactly
-// what a single launch on that problem computes.
+pgk_status launch_quant_fp8_grouped(int transpose, const GQuant* probs, const int* prefix, int G,
+                                    int total, uint8_t* dst, long long ldd, float* scales,
+                                    int ld_scales, cudaStream_t st);
+
+// G problems in a tensor-core form: one grouped conversion (BF16, split) or
+// quantisation (FP8) of all A operands, one of all B operands (transposed), both
+// into packed K-major workspaces, then one persistent tensor-core launch over the
+// tiles of every problem, problems in decreasing K order.  Problem g's operands
+// start at a multiple of 128 rows and are zero from K_g to the next multiple of the
+// K block (64; 128 for FP8, whose 128 x 128 scale blocks then coincide with those of
+// the problem alone), so every tile computes exactly what a single launch on that
+// problem computes.
 pgk_status tc_gemm_grouped(int G, const pgk_problem* pr, pgk_dtype dtype, const pgk_params* prog,
                            int beta, cudaStream_t s) {
-    pgk_params pp = {128, 128, dtype == PGK_BF16 ? 6 : 3, 0, 64};
+    const bool fp8 = dtype == PGK_FP8_E4M3, split = dtype == PGK_SPLIT_BF16;
+    const int kb = fp8 ? 128 : 64;            // K block of the form
+    pgk_params pp = {128, 128, dtype == PGK_SPLIT_BF16 ? 3 : 6, 0, kb};
     if (prog) pp = *prog;
-    if (pp.B0 != 128 || (pp.tile != 0 && pp.tile != 64)) {
-        set_error("grouped tensor-core tiles are 128 x B1 x 64 (B0=%d tile=%d)", pp.B0, pp.tile);
+    if (pp.B0 != 128 || (pp.tile != 0 && pp.tile != kb)) {
+        set_error("grouped tensor-core tiles are 128 x B1 x %d (B0=%d tile=%d)", kb, pp.B0, pp.tile);
         return PGK_ERR_UNSUPPORTED;
     }
     int nv;
@@ -969,6 +981,8 @@ pgk_status tc_gemm_grouped(int G, const pgk_problem* pr, pgk_dtype dtype, const 
     std::vector<int> order(G);
     for (int i = 0; i < G; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pr[a].K > pr[b].K; });
+    // items of the operand preparation: 64 x 64 tiles (BF16, split), 128 x 128 (FP8)
+    const int it = fp8 ? 128 : 64;
     int kmax = 0;
     long long rowsA = 0, rowsB = 0, tiles = 0, itemsA = 0, itemsB = 0;
     for (int i = 0; i < G; ++i) {
@@ -977,44 +991,50 @@ pgk_status tc_gemm_grouped(int G, const pgk_problem* pr, pgk_dtype dtype, const 
         rowsA += (q.M + 127) / 128 * 128;
         rowsB += (q.N + 127) / 128 * 128;
         tiles += (long long)((q.M + 127) / 128) * ((q.N + v->BN - 1) / v->BN);
-        const long long kr = (q.K + 63) / 64;
-        itemsA += (long long)((q.M + 63) / 64) * kr;
-        itemsB += kr * ((q.N + 63) / 64);
+        const long long kr = (q.K + kb - 1) / kb * kb / it;
+        itemsA += (long long)((q.M + it - 1) / it) * kr;
+        itemsB += kr * ((q.N + it - 1) / it);
     }
-    const long long kst = (long long)(kmax + 63) / 64 * 64;   // row stride of the packed operands
+    const long long kst = (long long)(kmax + kb - 1) / kb * kb;   // row stride of the packed operands
     if (rowsA > INT_MAX - 256 || rowsB > INT_MAX - 256 || tiles > INT_MAX || itemsA > INT_MAX ||
-        itemsB > INT_MAX) {
+        itemsB > INT_MAX || kst > INT_MAX) {
         set_error("grouped tensor-core problem set too large for one launch");
         return PGK_ERR_INVALID_ARG;
     }
-    // host image of the tables: TcProb[G] | GCvt A[G] | GCvt B[G] | int4 tiles[T] |
+    // host image of the tables: TcProb[G] | prep A[G] | prep B[G] | int4 tiles[T] |
     // int prefixA[G+1] | int prefixB[G+1]
+    const size_t esz_prep = fp8 ? sizeof(GQuant) : sizeof(GCvt);
     const size_t off_gA = (sizeof(TcProb) * G + 15) / 16 * 16;
-    const size_t off_gB = off_gA + (sizeof(GCvt) * G + 15) / 16 * 16;
-    const size_t off_t = off_gB + (sizeof(GCvt) * G + 15) / 16 * 16;
+    const size_t off_gB = off_gA + (esz_prep * G + 15) / 16 * 16;
+    const size_t off_t = off_gB + (esz_prep * G + 15) / 16 * 16;
     const size_t off_pA = off_t + sizeof(int4) * (size_t)tiles;
     const size_t off_pB = off_pA + (sizeof(int) * (G + 1) + 15) / 16 * 16;
     const size_t bytes = off_pB + sizeof(int) * (G + 1);
     std::vector<unsigned char> img(bytes, 0);
     TcProb* tp = reinterpret_cast<TcProb*>(img.data());
-    GCvt* ga = reinterpret_cast<GCvt*>(img.data() + off_gA);
-    GCvt* gb = reinterpret_cast<GCvt*>(img.data() + off_gB);
     int4* tl = reinterpret_cast<int4*>(img.data() + off_t);
     int* pa = reinterpret_cast<int*>(img.data() + off_pA);
     int* pb = reinterpret_cast<int*>(img.data() + off_pB);
     long long ra = 0, rb = 0, t = 0, ia = 0, ib = 0;
     for (int j = 0; j < G; ++j) {
         const pgk_problem& q = pr[order[j]];
-        const int kr = (q.K + 63) / 64 * 64;
+        const int kr = (q.K + kb - 1) / kb * kb;
         tp[j] = TcProb{q.C, q.M, q.N, q.K, q.ldc, (int)ra, (int)rb};
         const int va = ((uintptr_t)q.A % 16 == 0) && q.lda % 4 == 0;
         const int vb = ((uintptr_t)q.B % 16 == 0) && q.ldb % 4 == 0;
-        ga[j] = GCvt{q.A, q.lda, q.M, q.K, kr, va, 0, ra};
-        gb[j] = GCvt{q.B, q.ldb, q.K, q.N, kr, vb, 0, rb};
+        if (fp8) {
+            reinterpret_cast<GQuant*>(img.data() + off_gA)[j] =
+                GQuant{q.A, q.lda, q.M, q.K, kr, va, (int)(ra / 128), ra};
+            reinterpret_cast<GQuant*>(img.data() + off_gB)[j] =
+                GQuant{q.B, q.ldb, q.K, q.N, kr, vb, (int)(rb / 128), rb};
+        } else {
+            reinterpret_cast<GCvt*>(img.data() + off_gA)[j] = GCvt{q.A, q.lda, q.M, q.K, kr, va, 0, ra};
+            reinterpret_cast<GCvt*>(img.data() + off_gB)[j] = GCvt{q.B, q.ldb, q.K, q.N, kr, vb, 0, rb};
+        }
         pa[j] = (int)ia;
         pb[j] = (int)ib;
-        ia += (long long)((q.M + 63) / 64) * (kr / 64);
-        ib += (long long)(kr / 64) * ((q.N + 63) / 64);
+        ia += (long long)((q.M + it - 1) / it) * (kr / it);
+        ib += (long long)(kr / it) * ((q.N + it - 1) / it);
         const int tm_n = (q.M + 127) / 128, tn_n = (q.N + v->BN - 1) / v->BN;
         for (int tm = 0; tm < tm_n; ++tm)
             for (int tn = 0; tn < tn_n; ++tn) tl[t++] = make_int4(j, tm, tn, 0);
@@ -1026,40 +1046,62 @@ pgk_status tc_gemm_grouped(int G, const pgk_problem* pr, pgk_dtype dtype, const 
 
     unsigned char* dt = (unsigned char*)workspace(WS_TABLE, bytes, &st);
     if (!dt) return st;
-    const bool split = dtype == PGK_SPLIT_BF16;
-    const size_t abytes = (size_t)rowsA * kst * 2, bbytes = (size_t)rowsB * kst * 2;
-    uint16_t* a0 = (uint16_t*)workspace(WS_A0, abytes, &st);
+    const int esz = fp8 ? 1 : 2;
+    const size_t abytes = (size_t)rowsA * kst * esz, bbytes = (size_t)rowsB * kst * esz;
+    void* a0 = workspace(WS_A0, abytes, &st);
     if (!a0) return st;
-    uint16_t* b0 = (uint16_t*)workspace(WS_B0, bbytes, &st);
+    void* b0 = workspace(WS_B0, bbytes, &st);
     if (!b0) return st;
-    uint16_t* a1 = nullptr;
-    uint16_t* b1 = nullptr;
+    void* a1 = nullptr;
+    void* b1 = nullptr;
+    float* sa = nullptr;
+    float* sb = nullptr;
     if (split) {
-        if (!(a1 = (uint16_t*)workspace(WS_A1, abytes, &st))) return st;
-        if (!(b1 = (uint16_t*)workspace(WS_B1, bbytes, &st))) return st;
+        if (!(a1 = workspace(WS_A1, abytes, &st))) return st;
+        if (!(b1 = workspace(WS_B1, bbytes, &st))) return st;
+    }
+    if (fp8) {
+        if (!(sa = (float*)workspace(WS_SA, (size_t)(rowsA / 128) * (kst / 128) * 4, &st))) return st;
+        if (!(sb = (float*)workspace(WS_SB, (size_t)(kst / 128) * (rowsB / 128) * 4, &st))) return st;
     }
     PGK_CUDA_TRY(cudaMemcpyAsync(dt, img.data(), bytes, cudaMemcpyHostToDevice, s), "table upload");
-    const int mode = split ? 1 : 0;
-    if ((st = launch_cvt_grouped(mode, 0, reinterpret_cast<const GCvt*>(dt + off_gA),
-                                 reinterpret_cast<const int*>(dt + off_pA), G, (int)itemsA, a0, a1, kst,
-                                 s)) != PGK_OK)
-        return st;
-    if ((st = launch_cvt_grouped(mode, 1, reinterpret_cast<const GCvt*>(dt + off_gB),
-                                 reinterpret_cast<const int*>(dt + off_pB), G, (int)itemsB, b0, b1, kst,
-                                 s)) != PGK_OK)
-        return st;
+    if (fp8) {
+        if ((st = launch_quant_fp8_grouped(0, reinterpret_cast<const GQuant*>(dt + off_gA),
+                                           reinterpret_cast<const int*>(dt + off_pA), G, (int)itemsA,
+                                           (uint8_t*)a0, kst, sa, (int)(kst / 128), s)) != PGK_OK)
+            return st;
+        if ((st = launch_quant_fp8_grouped(1, reinterpret_cast<const GQuant*>(dt + off_gB),
+                                           reinterpret_cast<const int*>(dt + off_pB), G, (int)itemsB,
+                                           (uint8_t*)b0, kst, sb, (int)(rowsB / 128), s)) != PGK_OK)
+            return st;
+    } else {
+        const int mode = split ? 1 : 0;
+        if ((st = launch_cvt_grouped(mode, 0, reinterpret_cast<const GCvt*>(dt + off_gA),
+                                     reinterpret_cast<const int*>(dt + off_pA), G, (int)itemsA,
+                                     (uint16_t*)a0, (uint16_t*)a1, kst, s)) != PGK_OK)
+            return st;
+        if ((st = launch_cvt_grouped(mode, 1, reinterpret_cast<const GCvt*>(dt + off_gB),
+                                     reinterpret_cast<const int*>(dt + off_pB), G, (int)itemsB,
+                                     (uint16_t*)b0, (uint16_t*)b1, kst, s)) != PGK_OK)
+            return st;
+    }
     CUtensorMap ma, mb, ma2, mb2;
-    if ((st = make_map(&ma, a0, (int)rowsA, (int)kst, (int)kst, 2, 128)) != PGK_OK) return st;
-    if ((st = make_map(&mb, b0, (int)rowsB, (int)kst, (int)kst, 2, v->BN)) != PGK_OK) return st;
+    if ((st = make_map(&ma, a0, (int)rowsA, (int)kst, (int)kst, esz, 128)) != PGK_OK) return st;
+    if ((st = make_map(&mb, b0, (int)rowsB, (int)kst, (int)kst, esz, v->BN)) != PGK_OK) return st;
     if (split) {
-        if ((st = make_map(&ma2, a1, (int)rowsA, (int)kst, (int)kst, 2, 128)) != PGK_OK) return st;
-        if ((st = make_map(&mb2, b1, (int)rowsB, (int)kst, (int)kst, 2, v->BN)) != PGK_OK) return st;
+        if ((st = make_map(&ma2, a1, (int)rowsA, (int)kst, (int)kst, esz, 128)) != PGK_OK) return st;
+        if ((st = make_map(&mb2, b1, (int)rowsB, (int)kst, (int)kst, esz, v->BN)) != PGK_OK) return st;
     } else {
         ma2 = ma;
         mb2 = mb;
     }
     TcParams p;
     memset(&p, 0, sizeof(p));
+    // FP8: the scale arrays' row strides (ceil(K/128) and ceil(N/128) of a single launch)
+    p.K = (int)kst;
+    p.N = (int)rowsB;
+    p.sA = sa;
+    p.sB = sb;
     p.beta = beta ? 1 : 0;
     p.err = device_error_word(&st);
     if (!p.err) return st;

@@ -19,6 +19,8 @@ errmeas    the FP64 error reduction on 8192^2 (GB/s).
 mlp        the cost-model kernels (forward, minibatch gradient + Adam, full gradient).
 forms      every form (FP32, BF16, split, FP8) at 4096^3, 8192 x 1024 x 4096 and
            16384 x 64 x 16384: step and kernel time, error on 64 sampled rows.
+link       the host link with pinned buffers (256 MiB copies: host-to-device, device-to-host,
+           both at once) and the end-to-end step of pgk_gemm_host at 8192^3 (split form).
 peaks      the library's FP32 FMA probe (paired and scalar) with the SM clock during it,
            and, as context only, PyTorch's BF16 matmul and FP8 scaled matmul at 8192^3.
 precision  8192^3, normal(0,1) and row-scaled by 10^uniform(-3,3): every form's step
@@ -179,7 +181,8 @@ def grouped(dev, stream):
     tc = {}
     for name, dt, prog in (("bf16", pgk.BF16, pgk.params(128, 128, 6, 0, 64)),
                            ("split", pgk.SPLIT_BF16, pgk.params(128, 128, 3, 0, 64)),
-                           ("split3", pgk.SPLIT_BF16, pgk.params(128, 128, 6, 0, 64))):
+                           ("split3", pgk.SPLIT_BF16, pgk.params(128, 128, 6, 0, 64)),
+                           ("fp8", pgk.FP8_E4M3, pgk.params(128, 128, 6, 0, 128))):
         run = lambda: pgk.gemm_grouped(probs, dt, prog, stream=sh)
         run()
         ms = _events_ms(run, 10, stream)
@@ -468,6 +471,63 @@ def peaks(dev, stream):
     return out
 
 
+def link(dev, stream):
+    """Host-link bandwidth with pinned buffers (PyTorch copies, timed with events on
+    the copy streams) and the end-to-end step time of pgk_gemm_host at 8192^3."""
+    import torch
+    n = 64 * 1024 * 1024                       # 256 MiB of float32
+    h_in = torch.empty(n).pin_memory()
+    h_out = torch.empty(n).pin_memory()
+    d_in = torch.empty(n, device=dev)
+    d_out = torch.empty(n, device=dev)
+    s2 = torch.cuda.Stream(device=dev)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            best = min(best, (time.perf_counter() - t0) * 1e3)
+        return best
+
+    def h2d():
+        with torch.cuda.stream(stream):
+            d_in.copy_(h_in, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_out, non_blocking=True)
+
+    gb = n * 4 / 1e9
+    out = {"config": "host link, pinned 256 MiB copies"}
+    out["h2d_gbs"] = gb / timed(h2d) * 1e3
+    out["d2h_gbs"] = gb / timed(d2h) * 1e3
+    out["duplex_gbs_total"] = 2 * gb / timed(lambda: (h2d(), d2h())) * 1e3
+    del h_in, h_out, d_in, d_out
+    M = N = K = 8192
+    A, B = inputs.gemm_operands(M, N, K, seed=0)
+    Ah, Bh = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+    Ch = torch.empty(M, N).pin_memory()
+    prog = pgk.params(128, 256, 4, 0, 0)
+    call = lambda: pgk.gemm_host(Ah, Bh, Ch, pgk.SPLIT_BF16, prog, stream=stream.cuda_stream)
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    steps = 20
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        call()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    link_ms = (M * K + K * N + M * N) * 4 / 1e9 / out["duplex_gbs_total"] * 1e3
+    out.update({"gemm_host_split_ms_per_step": ms, "gemm_host_split_tflops": 2.0 * M * N * K / ms / 1e9,
+                "link_time_for_768MiB_at_duplex_ms": link_ms})
+    return out
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
@@ -485,7 +545,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     fns = {"config1": config1, "scale": scale, "grouped": grouped, "precision": precision,
            "mm": mm_table, "transpose": transpose_table, "jacobi": jacobi_table,
-           "errmeas": errmeas, "mlp": mlp_kernels, "peaks": peaks, "forms": forms}
+           "errmeas": errmeas, "mlp": mlp_kernels, "peaks": peaks, "forms": forms, "link": link}
     for w in args.which:
         t0 = time.time()
         with torch.cuda.stream(stream):

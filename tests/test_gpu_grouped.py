@@ -88,15 +88,17 @@ def test_invalid_problem_rejected(dev):
 
 TC_FORMS = [(pgk.BF16, pgk.params(128, 128, 6, 0, 64)),
             (pgk.SPLIT_BF16, pgk.params(128, 128, 3, 0, 64)),
-            (pgk.SPLIT_BF16, pgk.params(128, 128, 6, 0, 64))]
+            (pgk.SPLIT_BF16, pgk.params(128, 128, 6, 0, 64)),
+            (pgk.FP8_E4M3, pgk.params(128, 128, 6, 0, 128))]
 
 
 @pytest.mark.parametrize("dtype,prog", TC_FORMS)
 def test_tensor_core_group_equals_single_launches(dev, dtype, prog):
-    """The BF16 / split forms of a ragged group (sizes 1..300, odd K, unaligned
+    """The tensor-core forms of a ragged group (sizes 1..300, odd K, unaligned
     strides): every problem equals pgk_gemm on it with the same tile program, bit
     for bit, for beta = 0 and 1 (packed operands at 128-row offsets, K zero-padded
-    to the 64-deep block: the same tile arithmetic as a single launch)."""
+    to the K block: the same tile arithmetic, and for FP8 the same 128 x 128 scale
+    blocks, as a single launch)."""
     rng = np.random.default_rng(11)
     dims = rng.integers(1, 300, size=(30, 3))
     dims[0] = (1, 1, 1)
