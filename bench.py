@@ -146,7 +146,7 @@ def run_reference(args):
 
     import oracle
     from paper_1801_04348_gb300 import inputs
-    M = N = K = args.size
+    M, N, K = gemm_shape(args)
     A, B = inputs.gemm_operands(M, N, K, seed=0)
     oracle.build()
     cores = oracle.max_threads()
@@ -188,6 +188,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="auto", choices=["auto", "f32", "split", "bf16", "fp8"])
     ap.add_argument("--size", type=int, default=8192)
+    ap.add_argument("--shape", default=None,
+                    help="M,N,K of the GEMM (default: --size for all three); other shapes than "
+                         "8192^3 are measurements beside the benchmark workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune-log", default=None, help="append the autotuner's CSV rows here")
@@ -212,7 +215,7 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    M = N = K = args.size
+    M, N, K = gemm_shape(args)
     A, B = inputs.gemm_operands(M, N, K, seed=rank)
     Ad = torch.from_numpy(A).to(dev)
     Bd = torch.from_numpy(B).to(dev)
@@ -285,7 +288,7 @@ def main():
 
     pk, pk_src = peaks()
     roof = roofline(form, alg, gemm_ms, ms / args.steps, machine, pk, pk_src, clocks,
-                    recorded_traffic(form, prog) if M == 8192 else None, timed_s=ms / 1e3)
+                    recorded_traffic(form, prog, (M, N, K)), timed_s=ms / 1e3)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(M, N, K, seed=0)
@@ -420,10 +423,18 @@ KERNEL_SOURCES = {"f32": ["simt_rb.cuh", "simt_f32.cu"], "split": ["tc_gemm.cu"]
                   "bf16": ["tc_gemm.cu"], "fp8": ["tc_gemm.cu"]}
 
 
-def recorded_traffic(form, prog):
+def gemm_shape(args):
+    if args.shape:
+        M, N, K = (int(x) for x in args.shape.split(","))
+        return M, N, K
+    return args.size, args.size, args.size
+
+
+def recorded_traffic(form, prog, shape):
     """DRAM bytes per GEMM launch from the committed ncu summary
     profiles/traffic_<form>_<B0>-<B1>-<s>-<sr>-<tile>.txt, or None when that
-    summary is missing or the kernel source changed since it was taken."""
+    summary is missing, was taken on another shape, or the kernel source changed
+    since it was taken."""
     import hashlib
     tag = "-".join(str(x) for x in prog.as_tuple())
     path = os.path.join(ROOT, "profiles", f"traffic_{form}_{tag}.txt")
@@ -442,6 +453,8 @@ def recorded_traffic(form, prog):
     if rec.get("source_sha1") != h.hexdigest():
         return None
     if rec.get("program_params") != ",".join(str(x) for x in prog.as_tuple()):
+        return None
+    if rec.get("shape") != ",".join(str(x) for x in shape):
         return None
     try:
         return float(rec["dram_bytes_per_launch"])

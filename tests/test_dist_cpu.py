@@ -51,3 +51,26 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(0.25, None, 1) == 0.25
     assert bench.whole_job_tflops(1e12, 0.5, 1) == pytest.approx(2.0)
+
+
+def test_recorded_traffic_matches_workload_and_program():
+    """The roofline's DRAM traffic comes from a committed capture only for the
+    workload and program it was taken on (and while the kernel source is unchanged)."""
+    import bench
+    from paper_1801_04348_gb300 import pgk
+    prog = pgk.params(128, 256, 4, 0, 0)
+    assert bench.recorded_traffic("split", prog, (4096, 4096, 4096)) is None
+    assert bench.recorded_traffic("split", prog, (8192, 8192, 4096)) is None
+    assert bench.recorded_traffic("split", pgk.params(128, 256, 5, 0, 0), (8192, 8192, 8192)) is None
+    t = bench.recorded_traffic("split", prog, (8192, 8192, 8192))
+    assert t is None or t > 8e8    # at least the compulsory bytes of one launch
+
+
+def test_shape_option():
+    import bench
+
+    class A:
+        shape, size = None, 4096
+    assert bench.gemm_shape(A) == (4096, 4096, 4096)
+    A.shape = "16384,64,16384"
+    assert bench.gemm_shape(A) == (16384, 64, 16384)

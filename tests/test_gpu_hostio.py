@@ -112,3 +112,16 @@ def test_device_pointers_are_rejected(dev):
     with pytest.raises(pgk.PgkError) as e:
         pgk.gemm_host(A, Bh, Bh.clone(), pgk.F32)
     assert e.value.status == 1  # PGK_ERR_INVALID_ARG
+
+
+def test_pageable_inputs(dev):
+    """Pageable (not pinned) A, B and C go through the driver's staged copies and give
+    the same result."""
+    M, N, K = 384, 200, 257
+    A, B = inputs.gemm_operands(M, N, K, seed=31)
+    prog = pgk.params(16, 16, 8, 8, 8)
+    Ah, Bh = _host(A, False), _host(B, False)
+    Ch = _host(np.zeros((M, N), np.float32), False)
+    pgk.gemm_host(Ah, Bh, Ch, pgk.F32, prog)
+    torch.cuda.synchronize()
+    assert np.array_equal(Ch.numpy(), _device_result(dev, A, B, pgk.F32, prog))
