@@ -188,7 +188,8 @@ static cudaError_t launch_rb(const SimtArgs& p, int, cudaStream_t st) {
         (long long)((p.M + Cfg::BM - 1) / Cfg::BM) * ((p.N + Cfg::BN - 1) / Cfg::BN);
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     // Fewer output tiles than the GPU holds resident blocks, on a long K: split K
-    // so that every SM is filled (slices of at least 1024, a multiple of BK).
+    // into as many slices as still fit in one wave of resident blocks (slices of at
+    // least 1024, a multiple of BK); a wave and a few blocks would cost two waves.
     pgk_machine m;
     int splits = 1;
     if (p.K >= 4096 && current_machine(&m, NULL) == PGK_OK) {
@@ -206,7 +207,7 @@ static cudaError_t launch_rb(const SimtArgs& p, int, cudaStream_t st) {
         }
         const long long slots = (long long)std::max(per_sm, 1) * m.sm_count;
         if (tiles < slots) {
-            splits = (int)std::min<long long>((slots + tiles - 1) / tiles, 16);
+            splits = (int)std::min<long long>(slots / tiles, 16);
             splits = std::min(splits, p.K / 1024);
         }
     }
