@@ -517,8 +517,8 @@ def measure_e2e(form, prog, A, B, M, N, K, dev, stream, pgk, torch, args, ws):
             "h2d_bytes_per_step": (M * K + K * N) * 4, "d2h_bytes_per_step": M * N * 4,
             "steps": steps, "ms_per_step": ms, "api": "pgk_gemm_host (pinned host A, B, C)",
             "pipelining": "input copies of step i+1 on the library's stream overlap the GEMM of step i; "
-                          "the GEMM runs in two row panels and the first panel's C is copied back "
-                          "while the second computes",
+                          "the GEMM runs in row panels of whole tile rounds and each panel's C is "
+                          "copied back while the next panel computes",
             "timing": "host clock, device idle before the first call, synchronised after the last"}
 
 
