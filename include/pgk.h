@@ -91,9 +91,12 @@ typedef struct {
  *    per thread along M; sr = 1 is the paper's granularity, sr > 1 selects the
  *    register-blocked family), tile = BK, the depth of the shared-memory K tile
  *    (0 = the paper's choice BK = B0).
- *  Tensor-core forms: B0 x B1 is the CTA tile (B0 = 128; B1 in {128, 256}),
- *    s = number of pipeline stages, sr unused (0), tile = K depth per stage
- *    (0 = natural: 64 for BF16/split, 128 for FP8). */
+ *  Tensor-core forms: B0 x B1 is the output tile: B0 = 128 (one CTA per tile,
+ *    B1 in {128, 256}) or B0 = 256 (BF16 and split only: B1 = 256, a cluster of
+ *    two CTAs on the two SMs of a TPC per tile, each staging its 128 rows of A
+ *    and half of the B^T rows, one tcgen05.mma with cta_group::2 and M = 256 for
+ *    both); s = number of pipeline stages, sr unused (0), tile = K depth per
+ *    stage (0 = natural: 64 for BF16/split, 128 for FP8). */
 typedef struct { int B0, B1, s, sr, tile; } pgk_params;
 
 /* Leaves of the case discussion, with the paper's labels (Section 5):
@@ -216,7 +219,7 @@ PGK_API pgk_status pgk_gemm(int M, int N, int K, pgk_dtype dtype, const float* A
  * on a stream of its own, then runs the GEMM on `stream`; consecutive calls
  * alternate the sets, so the input copies of one call run while the GEMM of the
  * previous call computes.  The GEMM runs in row panels (boundaries at multiples
- * of 128 rows, panels of whole rounds of tiles for the SM count, at most 8; the
+ * of the tile height B0, panels of whole rounds of tiles for the SM count, at most 8; the
  * tensor-core forms convert B once) into a device buffer; each panel's C is
  * copied back on a second library stream while the next panel computes, and
  * `stream` waits for the copies.  Pinned

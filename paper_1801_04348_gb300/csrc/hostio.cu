@@ -93,19 +93,20 @@ cudaMemoryType memory_type(const void* p) {
     return a.type;
 }
 
-// Row panels in 128-row tile rows: the smallest panel of at least 1/8 of the tile
-// rows whose tile count (panel rows x column tiles of width bn) is a multiple of
-// the SM count, repeated, the remainder last; else two halves.  Returns the
-// number of panels (<= 8) and their first rows in starts[0..n] (starts[n] = M).
-int plan_panels(int M, int N, int bn, int sms, int* starts) {
-    const int T = (M + 127) / 128, tn = (N + bn - 1) / bn;
+// Row panels in tile rows of bm rows (128, or 256 for CTA-pair tiles): the
+// smallest panel of at least 1/8 of the tile rows whose tile count (panel rows x
+// column tiles of width bn) is a multiple of the number of tile slots (SMs, or
+// SM pairs), repeated, the remainder last; else two halves.  Returns the number
+// of panels (<= 8) and their first rows in starts[0..n] (starts[n] = M).
+int plan_panels(int M, int N, int bm, int bn, int slots, int* starts) {
+    const int T = (M + bm - 1) / bm, tn = (N + bn - 1) / bn;
     int r = 0;
-    if (T >= 2 && sms > 0)
+    if (T >= 2 && slots > 0)
         for (int c = std::max(1, (T + 7) / 8); c <= T / 2 && !r; ++c)
-            if (((long long)c * tn) % sms == 0) r = c;
+            if (((long long)c * tn) % slots == 0) r = c;
     if (!r) r = T >= 2 ? (T + 1) / 2 : T;
     int n = 0;
-    for (int t = 0; t < T; t += r) starts[n++] = t * 128;
+    for (int t = 0; t < T; t += r) starts[n++] = t * bm;
     starts[n] = M;
     return n;
 }
@@ -196,8 +197,9 @@ pgk_status pgk_gemm_host(int M, int N, int K, pgk_dtype dtype, const float* A, i
     PGK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     const bool tc = dtype == PGK_BF16 || dtype == PGK_SPLIT_BF16 || dtype == PGK_FP8_E4M3;
     const int bn = tc ? (prog ? prog->B1 : 256) : (prog ? std::max(1, prog->B1 * prog->s) : 128);
+    const int bm = tc && prog && prog->B0 == 256 ? 256 : 128;
     int starts[9];
-    const int np = plan_panels(M, N, bn, sms, starts);
+    const int np = plan_panels(M, N, bm, bn, sms / (bm / 128), starts);
     for (int i = 0; i < np && s == PGK_OK; ++i) {
         const int r0 = starts[i], rows = starts[i + 1] - r0;
         s = gemm_device(rows, N, K, dtype, set.A + (size_t)r0 * K, K, set.B, N, set.C + (size_t)r0 * N, N,

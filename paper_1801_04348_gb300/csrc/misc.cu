@@ -149,20 +149,24 @@ static int simt_candidates(int rb_family, pgk_params* out, int cap) {
 
 static int tc_candidates(pgk_dtype dtype, pgk_params* out, int cap) {
     std::vector<pgk_params> c;
+    // B0 = 256: a CTA pair per 256 x 256 tile (each SM stages half of B)
     if (dtype == PGK_SPLIT_BF16) {
         pgk_params a = {128, 128, 3, 0, 0}, b = {128, 256, 2, 0, 0}, d = {128, 256, 4, 0, 0},
-                   e = {128, 128, 6, 0, 0};
+                   e = {128, 128, 6, 0, 0}, f = {256, 256, 3, 0, 0}, g = {256, 256, 6, 0, 0};
         c.push_back(a);
         c.push_back(b);
         c.push_back(d);
         c.push_back(e);
+        c.push_back(f);
+        c.push_back(g);
     } else if (dtype == PGK_BF16) {
         pgk_params a = {128, 256, 4, 0, 0}, b = {128, 128, 6, 0, 0}, d = {128, 256, 3, 0, 0},
-                   e = {128, 128, 4, 0, 0};
+                   e = {128, 128, 4, 0, 0}, f = {256, 256, 6, 0, 0};
         c.push_back(a);
         c.push_back(b);
         c.push_back(d);
         c.push_back(e);
+        c.push_back(f);
     } else {
         pgk_params a = {128, 128, 6, 0, 0}, b = {128, 256, 4, 0, 0};
         c.push_back(a);

@@ -45,15 +45,19 @@ static constexpr unsigned int ERR_TIMEOUT_EPILOGUE = 0x4u;
 static constexpr unsigned int ERR_TIMEOUT_DRAIN = 0x8u;
 static constexpr unsigned int ERR_TIMEOUT_SELFTEST = 0x10u;
 
-template <int MODE_, int BN_, int STAGES_>
+template <int MODE_, int BN_, int STAGES_, bool PAIR_ = false>
 struct TcCfg {
     static constexpr int MODE = MODE_, BN = BN_, STAGES = STAGES_;
-    static constexpr int BM = 128;
+    static constexpr bool PAIR = PAIR_;
+    static constexpr int BM = 128;                          // rows of A staged (and accumulated) per CTA
+    static constexpr int CTAS = PAIR ? 2 : 1;               // CTAs sharing one output tile
+    static constexpr int TM = BM * CTAS;                    // rows of an output tile
+    static constexpr int BNL = BN / CTAS;                   // rows of B^T staged per CTA
     static constexpr int BK = MODE == MODE_FP8 ? 128 : 64;   // elements per stage row (128 bytes)
     static constexpr int UK = MODE == MODE_FP8 ? 32 : 16;    // K per MMA instruction
     static constexpr int NKSUB = BK / UK;                   // MMAs per stage and product
     static constexpr int A_BYTES = BM * 128;
-    static constexpr int B_BYTES = BN * 128;
+    static constexpr int B_BYTES = BNL * 128;
     static constexpr int NOPS = MODE == MODE_SPLIT ? 2 : 1; // hi/lo pairs per stage
     static constexpr int PASSES = MODE == MODE_SPLIT3 ? 3 : 1;  // stages per K block
     static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
@@ -77,6 +81,7 @@ struct TcCfg {
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation is a power of two");
     static_assert(SMEM <= 232448 - 512, "stage ring, staging blocks and barriers fit the opt-in shared memory");
     static_assert(CHUNK == 0 || BN / (EPI_WARPS / 4) <= 128, "promoted columns per warp");
+    static_assert(!PAIR || (MODE != MODE_FP8 && BN == 256), "CTA pairs: kind::f16 forms, 256 x 256 tiles");
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -235,6 +240,85 @@ __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// ---------------------------------------------- CTA pairs (cta_group::2)
+// First tile and tile stride of this CTA's work unit (a CTA, or a CTA pair).
+template <bool PAIR>
+__device__ __forceinline__ int tile_first() {
+    return PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+}
+template <bool PAIR>
+__device__ __forceinline__ unsigned tile_stride() {
+    return PAIR ? gridDim.x >> 1 : gridDim.x;
+}
+__device__ __forceinline__ uint32_t cluster_ctarank();
+// rank of this CTA in its pair (0: the leader); 0 for single-CTA tiles
+template <bool PAIR>
+__device__ __forceinline__ uint32_t pair_rank() {
+    if constexpr (PAIR) return cluster_ctarank();
+    return 0u;
+}
+
+// Two CTAs of a cluster share one 256-row tile: each stages its own 128 rows of A
+// and its own half of the B^T rows, the even CTA (the leader) issues the MMAs,
+// which read both CTAs' shared tiles and write both CTAs' tensor memory.
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// TMA tile load into this CTA's shared memory whose completion is counted on an
+// mbarrier of either CTA of the pair (bar: shared::cluster address)
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar, int x,
+                                                 int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f16_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                             uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+// arrive on the mbarrier at this offset in both CTAs of the pair once the MMAs
+// issued so far have completed
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)), "h"((unsigned short)3)
+        : "memory");
+}
+
+// arrive on the leader's mbarrier only (the drain of an aborted launch)
+__device__ __forceinline__ void mma_commit_pair_local(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// arrive on an mbarrier of either CTA of the cluster (bar: shared::cluster address)
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // One problem of a grouped launch: its sizes, the first rows of its operands in
 // the packed workspaces (A: M rows, B^T: N rows, both K-major with zeros from K
 // to the next multiple of the K block) and its output.
@@ -249,6 +333,9 @@ struct TcParams {
     float* C;
     int ldc;
     int beta;
+    // tail balancing: the last `tail` tiles of the tile order run as two tiles of
+    // BN/2 columns each (set when they would otherwise fill at most half a round)
+    int tail;
     const float* sA;   // FP8: ceil(M/128) x ceil(K/128)
     const float* sB;   // FP8: ceil(K/128) x ceil(N/128)
     unsigned int* err;
@@ -258,11 +345,17 @@ struct TcParams {
     int ntiles_g;
 };
 
-template <class Cfg, bool GROUPED = false>
+// Tensor maps of one launch: A and B^T (hi, and lo for the split forms), and B^T
+// with half-height boxes for the column halves of tail-balanced tiles.
+struct TcMaps {
+    CUtensorMap a, b, a2, b2, bh, b2h;
+};
+
+// TAIL: the instantiation that runs the last p.tail tiles as column halves; the
+// others compile without any of that logic in their loops.
+template <class Cfg, bool GROUPED = false, bool TAIL = false>
 __global__ void __launch_bounds__(Cfg::THREADS, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
-              TcParams p) {
+    k_tc_gemm(const __grid_constant__ TcMaps tm, TcParams p) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[Cfg::STAGES];
     __shared__ uint64_t empty_bar[Cfg::STAGES];
@@ -272,14 +365,25 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
 
+    constexpr bool PAIR = Cfg::PAIR;
+    static_assert(!(PAIR && GROUPED), "grouped launches use single-CTA tiles");
+    static_assert(!TAIL || (!GROUPED && Cfg::BN == 256 && Cfg::MODE != MODE_FP8),
+                  "tail halves: 256-wide single launches of the BF16 and split forms");
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    // CTA pairs: rank 0 (the leader) issues the MMAs; the pair walks the tiles as one
+    // unit.  The unit's first tile, its stride and the CTA's rank are read where the
+    // roles use them (tile_first, tile_stride, pair_rank): copies taken here, before
+    // the barriers and the allocation, made every role about 10 % slower.
 
-    const int tiles_m = (p.M + Cfg::BM - 1) / Cfg::BM;
+    const int tiles_m = (p.M + Cfg::TM - 1) / Cfg::TM;
     const int tiles_n = (p.N + Cfg::BN - 1) / Cfg::BN;
-    const int ntiles = GROUPED ? p.ntiles_g : tiles_m * tiles_n;
+    const int nfull = tiles_m * tiles_n;
+    const int tail = TAIL ? p.tail : 0;
+    // work units: every tile, the last `tail` of them twice (one per column half)
+    const int ntiles = GROUPED ? p.ntiles_g : nfull + tail;
     const int nkb = (p.K + Cfg::BK - 1) / Cfg::BK;
 
     if (threadIdx.x == 0) {
@@ -289,27 +393,39 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         }
         for (int b = 0; b < Cfg::ACC_BUFS; ++b) {
             mbar_init(&accf_bar[b], 1);
-            mbar_init(&acce_bar[b], Cfg::EPI_WARPS);   // one arrival per epilogue warp
+            // one arrival per epilogue warp (of both CTAs of a pair, at the leader)
+            mbar_init(&acce_bar[b], Cfg::EPI_WARPS * Cfg::CTAS);
         }
         mbar_init(&drain_bar, 1);
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        tmap_prefetch(&tmA);
-        tmap_prefetch(&tmB);
+        tmap_prefetch(&tm.a);
+        tmap_prefetch(&tm.b);
         if (Cfg::MODE == MODE_SPLIT || Cfg::MODE == MODE_SPLIT3) {
-            tmap_prefetch(&tmA2);
-            tmap_prefetch(&tmB2);
+            tmap_prefetch(&tm.a2);
+            tmap_prefetch(&tm.b2);
         }
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&tmem_base_sh)),
-                     "r"((uint32_t)Cfg::TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        // a pair allocates collectively: one warp of each CTA, the same columns in both
+        if (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tmem_base_sh)),
+                         "r"((uint32_t)Cfg::TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tmem_base_sh)),
+                         "r"((uint32_t)Cfg::TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    // the peer's barriers are initialised before any copy, commit or arrival targets them
+    if (PAIR) cluster_sync();
     tc_fence_after();
     const uint32_t tmem_base = tmem_base_sh;
     volatile int* abort_flag = &abort_sh;
@@ -329,6 +445,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
     // output, and where its operands start in the packed workspaces (grouped)
     struct TileInfo {
         int tm, tn, M, N, nkb, rowA, rowB, ldc;
+        int half;   // -1: the whole tile; 0 or 1: its first or second BN/2 columns
         float* C;
     };
     auto tile_info = [&](int t) {
@@ -345,8 +462,16 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             ti.rowB = q->rowB;
             ti.ldc = q->ldc;
             ti.C = q->C;
+            ti.half = -1;
         } else {
-            coords(t, ti.tm, ti.tn);
+            int tt = t;
+            ti.half = -1;
+            if (TAIL && t >= nfull - tail) {
+                const int j = t - (nfull - tail);
+                tt = nfull - tail + (j >> 1);
+                ti.half = j & 1;
+            }
+            coords(tt, ti.tm, ti.tn);
             ti.M = p.M;
             ti.N = p.N;
             ti.nkb = nkb;
@@ -365,9 +490,18 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             uint32_t phase = 0;
             uint32_t issued_mask = 0, last_parity = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = tile_first<PAIR>(); t < ntiles && ok; t += tile_stride<PAIR>()) {
                 const TileInfo ti = tile_info(t);
-                const int ya = ti.rowA + ti.tm * Cfg::BM, yb = ti.rowB + ti.tn * Cfg::BN;
+                const bool hf = ti.half >= 0;
+                // B^T rows staged by this CTA: BNL, or BNL/2 for a column half
+                const int nb = hf ? Cfg::BNL / 2 : Cfg::BNL;
+                const uint32_t bytes = (uint32_t)(Cfg::NOPS * (Cfg::A_BYTES + nb * 128));
+                // this CTA's rows of A and of B^T (a pair splits both between its CTAs)
+                const int ya = ti.rowA + ti.tm * Cfg::TM + (int)pair_rank<PAIR>() * Cfg::BM;
+                const int yb = ti.rowB + ti.tn * Cfg::BN + (hf ? ti.half * (Cfg::BN / 2) : 0) +
+                               (int)pair_rank<PAIR>() * nb;
+                const CUtensorMap* mbh = hf ? &tm.bh : &tm.b;     // B^T hi
+                const CUtensorMap* mbl = hf ? &tm.b2h : &tm.b2;   // B^T lo
                 for (int kb = 0; kb < ti.nkb && ok; ++kb)
                 for (int v = 0; v < Cfg::PASSES; ++v) {
                     if (!mbar_wait(&empty_bar[stage], phase ^ 1u, abort_flag, p.err,
@@ -376,17 +510,31 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                         break;
                     }
                     uint8_t* st = tiles + (size_t)stage * Cfg::STAGE_BYTES;
-                    mbar_arrive_expect_tx(&full_bar[stage], Cfg::STAGE_BYTES);
                     const int x = kb * Cfg::BK;
                     // passes of MODE_SPLIT3: 0 = (A lo, B hi), 1 = (A hi, B lo), 2 = (A hi, B hi)
-                    const CUtensorMap* ma = (Cfg::MODE == MODE_SPLIT3 && v == 0) ? &tmA2 : &tmA;
-                    const CUtensorMap* mb = (Cfg::MODE == MODE_SPLIT3 && v == 1) ? &tmB2 : &tmB;
-                    tma_load_2d(st, ma, &full_bar[stage], x, ya);
-                    tma_load_2d(st + Cfg::A_BYTES, mb, &full_bar[stage], x, yb);
-                    if (Cfg::MODE == MODE_SPLIT) {
-                        tma_load_2d(st + Cfg::A_BYTES + Cfg::B_BYTES, &tmA2, &full_bar[stage], x, ya);
-                        tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tmB2, &full_bar[stage],
-                                    x, yb);
+                    const CUtensorMap* ma = (Cfg::MODE == MODE_SPLIT3 && v == 0) ? &tm.a2 : &tm.a;
+                    const CUtensorMap* mb = (Cfg::MODE == MODE_SPLIT3 && v == 1) ? mbl : mbh;
+                    if (PAIR) {
+                        // both CTAs' copies complete on the leader's barrier, which
+                        // the leader arms with the bytes of the pair
+                        const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0u);
+                        if (pair_rank<PAIR>() == 0) mbar_arrive_expect_tx(&full_bar[stage], bytes * 2);
+                        tma_load_2d_pair(st, ma, fb, x, ya);
+                        tma_load_2d_pair(st + Cfg::A_BYTES, mb, fb, x, yb);
+                        if (Cfg::MODE == MODE_SPLIT) {
+                            tma_load_2d_pair(st + Cfg::A_BYTES + Cfg::B_BYTES, &tm.a2, fb, x, ya);
+                            tma_load_2d_pair(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, mbl, fb, x, yb);
+                        }
+                    } else {
+                        mbar_arrive_expect_tx(&full_bar[stage], bytes);
+                        tma_load_2d(st, ma, &full_bar[stage], x, ya);
+                        tma_load_2d(st + Cfg::A_BYTES, mb, &full_bar[stage], x, yb);
+                        if (Cfg::MODE == MODE_SPLIT) {
+                            tma_load_2d(st + Cfg::A_BYTES + Cfg::B_BYTES, &tm.a2, &full_bar[stage], x,
+                                        ya);
+                            tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, mbl, &full_bar[stage],
+                                        x, yb);
+                        }
                     }
                     issued_mask |= 1u << stage;
                     last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
@@ -396,7 +544,14 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     }
                 }
             }
-            if (!ok) {
+            if (!ok && PAIR && pair_rank<PAIR>() != 0) {
+                // the peer's copies complete on the leader's barriers, which this CTA
+                // cannot observe: give copies in flight a bounded time to land (a tile
+                // copy takes microseconds) before the final cluster barrier
+                const unsigned long long t0 = globaltimer();
+                while (globaltimer() - t0 < 200000ULL) {
+                }
+            } else if (!ok) {
                 // drain: every issued copy must land before the CTA may exit
                 for (int s = 0; s < Cfg::STAGES; ++s)
                     if (issued_mask & (1u << s)) {
@@ -412,17 +567,24 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA
-        if (lane == 0) {
-            const uint32_t idesc = Cfg::MODE == MODE_FP8 ? idesc_e4m3(Cfg::BM, Cfg::BN)
-                                                         : idesc_bf16(Cfg::BM, Cfg::BN);
+        // one thread of the leader issues for the pair (M = 256: both CTAs' A rows,
+        // N = BN: both CTAs' halves of B^T, accumulators in both CTAs' tensor memory)
+        if (lane == 0 && pair_rank<PAIR>() == 0) {
+            // instruction descriptors of whole tiles and of column halves (N = BN/2)
+            const uint32_t idesc_full = Cfg::MODE == MODE_FP8 ? idesc_e4m3(Cfg::BM, Cfg::BN)
+                                                              : idesc_bf16(Cfg::TM, Cfg::BN);
+            const uint32_t idesc_half = Cfg::MODE == MODE_FP8 ? idesc_e4m3(Cfg::BM, Cfg::BN / 2)
+                                                              : idesc_bf16(Cfg::TM, Cfg::BN / 2);
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
             bool issued_any = false;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int tnkb = GROUPED ? tile_info(t).nkb : nkb;
+            for (int t = tile_first<PAIR>(); t < ntiles && ok; t += tile_stride<PAIR>()) {
+                const TileInfo ti = tile_info(t);
+                const int tnkb = ti.nkb;
+                const uint32_t idesc = ti.half >= 0 ? idesc_half : idesc_full;
                 if (Cfg::CHUNK == 0) {
                     if (!mbar_wait(&acce_bar[acc], acc_phase ^ 1u, abort_flag, p.err, ERR_TIMEOUT_MMA)) {
                         ok = false;
@@ -458,8 +620,18 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                             const uint32_t accum = (kin > 0 || v > 0 || ks > 0) ? 1u : 0u;
                             if (Cfg::MODE == MODE_FP8) {
                                 mma_f8(d, da, db, idesc, accum);
+                            } else if (PAIR && (Cfg::MODE == MODE_BF16 || Cfg::MODE == MODE_SPLIT3)) {
+                                mma_f16_pair(d, da, db, idesc, accum);
                             } else if (Cfg::MODE == MODE_BF16 || Cfg::MODE == MODE_SPLIT3) {
                                 mma_f16(d, da, db, idesc, accum);
+                            } else if (PAIR) {
+                                const uint32_t sa2 = sb + Cfg::B_BYTES;   // A lo
+                                const uint32_t sb2 = sa2 + Cfg::A_BYTES;  // B lo
+                                const uint64_t da2 = sdesc_k128(sa2 + koff);
+                                const uint64_t db2 = sdesc_k128(sb2 + koff);
+                                mma_f16_pair(d, da2, db, idesc, accum);
+                                mma_f16_pair(d, da, db2, idesc, 1u);
+                                mma_f16_pair(d, da, db, idesc, 1u);
                             } else {
                                 const uint32_t sa2 = sb + Cfg::B_BYTES;   // A lo
                                 const uint32_t sb2 = sa2 + Cfg::A_BYTES;  // B lo
@@ -472,7 +644,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                             }
                         }
                         issued_any = true;
-                        mma_commit(&empty_bar[stage]);
+                        if (PAIR)
+                            mma_commit_pair(&empty_bar[stage]);
+                        else
+                            mma_commit(&empty_bar[stage]);
                         if (++stage == Cfg::STAGES) {
                             stage = 0;
                             phase ^= 1u;
@@ -480,7 +655,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     }
                     if (!ok) break;
                     if (Cfg::CHUNK > 0 && (kin == Cfg::CHUNK - 1 || kb == tnkb - 1)) {
-                        mma_commit(&accf_bar[acc]);
+                        if (PAIR)
+                            mma_commit_pair(&accf_bar[acc]);
+                        else
+                            mma_commit(&accf_bar[acc]);
                         if (++acc == Cfg::ACC_BUFS) {
                             acc = 0;
                             acc_phase ^= 1u;
@@ -489,7 +667,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 }
                 if (!ok) break;
                 if (Cfg::CHUNK == 0) {
-                    mma_commit(&accf_bar[acc]);
+                    if (PAIR)
+                        mma_commit_pair(&accf_bar[acc]);
+                    else
+                        mma_commit(&accf_bar[acc]);
                     if (++acc == Cfg::ACC_BUFS) {
                         acc = 0;
                         acc_phase ^= 1u;
@@ -498,7 +679,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             }
             if (!ok && issued_any) {
                 // drain: all MMAs issued by this thread must finish before TMEM is freed
-                mma_commit(&drain_bar);
+                if (PAIR)
+                    mma_commit_pair_local(&drain_bar);
+                else
+                    mma_commit(&drain_bar);
                 const unsigned long long t0 = globaltimer();
                 while (!mbar_try_wait(&drain_bar, 0)) {
                     if (globaltimer() - t0 > WAIT_LIMIT_NS) {
@@ -537,15 +721,57 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         };
         const int ncol = Cfg::BN / (Cfg::EPI_WARPS / 4);  // columns handled by this warp
         const int col0 = (e >> 2) * ncol;
+        // releases an accumulator: one arrival per warp at the MMA issuer's barrier
+        // (the leader's, for the peer of a pair)
+        auto release = [&](int a) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (PAIR)
+                    mbar_arrive_cluster(mapa_shared(smem_u32(&acce_bar[a]), 0u));
+                else
+                    mbar_arrive(&acce_bar[a]);
+            }
+        };
         int acc = 0;
         uint32_t acc_phase = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int t = tile_first<PAIR>(); t < ntiles && ok; t += tile_stride<PAIR>()) {
             const TileInfo ti = tile_info(t);
             const int tm = ti.tm;
-            const int row0 = tm * Cfg::BM + q * 32;   // first of the 32 rows of this warp
-            const int n0 = ti.tn * Cfg::BN + col0;
+            // first of the 32 rows of this warp (TMEM lane quarter q of this CTA's rows)
+            const int row0 = tm * Cfg::TM + (int)pair_rank<PAIR>() * Cfg::BM + q * 32;
+            const int n0 = ti.tn * Cfg::BN + (ti.half >= 0 ? ti.half * (Cfg::BN / 2) : 0) + col0;
             const int tN = ti.N;
+            // columns of this warp inside the tile (a column half holds BN/2; the tail
+            // is only used with BN = 256, where the promoted forms' 128-column warps
+            // fall wholly inside or outside it); an idle warp still waits and releases
+            const int wcols = ti.half >= 0 ? max(0, min(ncol, Cfg::BN / 2 - col0)) : ncol;
+            if (wcols == 0) {
+                // an idle warp of a column half: releases each accumulator unread, so
+                // that the hot loops below keep their compile-time shapes
+                const int nrel = Cfg::CHUNK > 0 ? (ti.nkb + Cfg::CHUNK - 1) / max(Cfg::CHUNK, 1) : 1;
+                for (int ch = 0; ch < nrel; ++ch) {
+                    int w = 1;
+                    if (lane == 0)
+                        w = mbar_wait(&accf_bar[acc], acc_phase, abort_flag, p.err,
+                                      ERR_TIMEOUT_EPILOGUE) ? 1 : 0;
+                    w = __shfl_sync(0xffffffffu, w, 0);
+                    if (!w) {
+                        ok = false;
+                        break;
+                    }
+                    while (!mbar_try_wait(&accf_bar[acc], acc_phase)) {
+                    }
+                    tc_fence_after();
+                    release(acc);
+                    if (++acc == Cfg::ACC_BUFS) {
+                        acc = 0;
+                        acc_phase ^= 1u;
+                    }
+                }
+                continue;
+            }
             if (Cfg::CHUNK > 0) {
                 constexpr int NCOL = Cfg::BN / (Cfg::EPI_WARPS / 4);
                 // running FP32 sums as pairs: acc2[j] holds columns 2j, 2j + 1
@@ -616,9 +842,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                                        f2_pack(__uint_as_float(r[c][2 * j]), __uint_as_float(r[c][2 * j + 1])),
                                        sc2);
                     }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&acce_bar[acc]);
+                    release(acc);
                     if (++acc == Cfg::ACC_BUFS) {
                         acc = 0;
                         acc_phase ^= 1u;
@@ -648,8 +872,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 while (!mbar_try_wait(&accf_bar[acc], acc_phase)) {
                 }
                 tc_fence_after();
-#pragma unroll 1
-                for (int c = 0; c < ncol / 32; ++c) {
+                auto drain_block = [&](int c) {
                     uint32_t r[32];
                     tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) +
                                   (uint32_t)(acc * Cfg::BN + col0 + c * 32),
@@ -659,10 +882,15 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
                     store_block(v, row0, n0 + c * 32, ti.M, tN, ti.C, ti.ldc);
+                };
+                if (ti.half < 0) {
+#pragma unroll 1
+                    for (int c = 0; c < ncol / 32; ++c) drain_block(c);
+                } else {
+#pragma unroll 1
+                    for (int c = 0; c < wcols / 32; ++c) drain_block(c);
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce_bar[acc]);
+                release(acc);
                 if (++acc == Cfg::ACC_BUFS) {
                     acc = 0;
                     acc_phase ^= 1u;
@@ -673,11 +901,19 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
 
     tc_fence_before();
     __syncthreads();
+    // neither CTA of a pair leaves while the other may still arrive on its barriers
+    // or the leader's MMAs may still use its shared tiles and tensor memory
+    if (PAIR) cluster_sync();
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                     "r"((uint32_t)Cfg::TMEM_COLS)
-                     : "memory");
+        if (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                         "r"((uint32_t)Cfg::TMEM_COLS)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                         "r"((uint32_t)Cfg::TMEM_COLS)
+                         : "memory");
     }
 }
 
@@ -738,33 +974,96 @@ static pgk_status make_map(CUtensorMap* map, const void* base, int rows, int K, 
     return PGK_OK;
 }
 
-typedef cudaError_t (*tc_launch_fn)(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&,
-                                    const CUtensorMap&, const TcParams&, int grid, cudaStream_t);
+// Launches the persistent kernel over `tiles` output tiles on at most `sm_count`
+// SMs: one CTA per tile slot, or for CTA pairs one two-CTA cluster per slot, as
+// many clusters as can be resident at once.
+typedef cudaError_t (*tc_launch_fn)(const TcMaps&, const TcParams&, long long tiles, int sm_count,
+                                    cudaStream_t);
 
-template <class Cfg>
-static cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& a2,
-                             const CUtensorMap& b2, const TcParams& p, int grid, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_tc_gemm<Cfg>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+// Tail balancing: with U tile slots and T tiles, the last T mod U tiles would run
+// as a partly filled round; when they fill at most half of it, each is run as two
+// column halves (BN = 256 tiles of the BF16 and split forms), so that round takes
+// about half as long.  Every output element is computed with the same products in
+// the same order.
+static int tail_tiles(long long tiles, long long slots, int BN) {
+    if (BN != 256 || slots < 2) return 0;
+    const long long rem = tiles % slots;
+    return (rem > 0 && 2 * rem <= slots) ? (int)rem : 0;
+}
+
+template <class Cfg, bool GROUPED>
+static cudaError_t launch_tc(const TcMaps& maps, const TcParams& p0, long long tiles, int sm_count,
+                             cudaStream_t st) {
+    const void* fn = (const void*)k_tc_gemm<Cfg, GROUPED>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     if (e != cudaSuccess) return e;
-    k_tc_gemm<Cfg><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a, b, a2, b2, p);
-    return cudaGetLastError();
+    TcParams p = p0;
+    p.tail = 0;
+    // the tail-balanced instantiation exists for 256-wide single launches of the
+    // BF16 and split forms; the FP8 form's per-chunk fold takes as long for a
+    // column half as for a whole tile, so halves would not shorten its last round
+    constexpr bool CAN_TAIL = !GROUPED && Cfg::BN == 256 && Cfg::MODE != MODE_FP8;
+    const void* fn_tail = fn;
+    if constexpr (CAN_TAIL) {
+        fn_tail = (const void*)k_tc_gemm<Cfg, false, true>;
+        e = cudaFuncSetAttribute(fn_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    if (!Cfg::PAIR) {
+        if (CAN_TAIL) p.tail = tail_tiles(tiles, sm_count, Cfg::BN);
+        const int grid = (int)std::min<long long>(tiles + p.tail, sm_count);
+        if constexpr (CAN_TAIL) {
+            if (p.tail > 0) {
+                k_tc_gemm<Cfg, false, true><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(maps, p);
+                return cudaGetLastError();
+            }
+        }
+        k_tc_gemm<Cfg, GROUPED><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(maps, p);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(sm_count / 2 * 2), 1, 1);
+    cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = Cfg::SMEM;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
+    if (e != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    clusters = std::min(clusters, sm_count / 2);
+    if (CAN_TAIL) p.tail = tail_tiles(tiles, clusters, Cfg::BN);
+    clusters = (int)std::min<long long>(tiles + p.tail, clusters);
+    cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+    if constexpr (CAN_TAIL) {
+        if (p.tail > 0) return cudaLaunchKernelEx(&cfg, k_tc_gemm<Cfg, false, true>, maps, p);
+    }
+    return cudaLaunchKernelEx(&cfg, k_tc_gemm<Cfg, GROUPED>, maps, p);
 }
 
 struct TcVariant {
-    int family, BN, stages, smem, threads, tmem_cols;
+    int family, BM, BN, stages, smem, threads, tmem_cols;
+    int b_box;   // rows of B^T per tensor-map box (per CTA)
     const void* func;
     tc_launch_fn launch;
 };
 
-template <int MODE, int BN, int ST>
+template <int MODE, int BN, int ST, bool PAIR = false>
 static TcVariant tcv(int family) {
-    typedef TcCfg<MODE, BN, ST> Cfg;
-    TcVariant v = {family, BN, ST, Cfg::SMEM, Cfg::THREADS, Cfg::TMEM_COLS,
-                   (const void*)k_tc_gemm<Cfg>, launch_tc<Cfg>};
+    typedef TcCfg<MODE, BN, ST, PAIR> Cfg;
+    TcVariant v = {family, Cfg::TM, BN, ST, Cfg::SMEM, Cfg::THREADS, Cfg::TMEM_COLS, Cfg::BNL,
+                   (const void*)k_tc_gemm<Cfg>, launch_tc<Cfg, false>};
     return v;
 }
 
+// B0 = 128: one CTA per 128 x B1 tile; B0 = 256: a CTA pair per 256 x 256 tile
 static const TcVariant* tc_table(int* n) {
     static const TcVariant t[] = {
         tcv<MODE_BF16, 256, 4>(PGK_FAM_TC_BF16),   tcv<MODE_BF16, 128, 6>(PGK_FAM_TC_BF16),
@@ -772,6 +1071,9 @@ static const TcVariant* tc_table(int* n) {
         tcv<MODE_SPLIT, 128, 3>(PGK_FAM_TC_SPLIT), tcv<MODE_SPLIT, 256, 2>(PGK_FAM_TC_SPLIT),
         tcv<MODE_SPLIT3, 256, 4>(PGK_FAM_TC_SPLIT), tcv<MODE_SPLIT3, 128, 6>(PGK_FAM_TC_SPLIT),
         tcv<MODE_FP8, 128, 6>(PGK_FAM_TC_FP8),     tcv<MODE_FP8, 256, 4>(PGK_FAM_TC_FP8),
+        tcv<MODE_BF16, 256, 6, true>(PGK_FAM_TC_BF16),
+        tcv<MODE_SPLIT3, 256, 6, true>(PGK_FAM_TC_SPLIT),
+        tcv<MODE_SPLIT, 256, 3, true>(PGK_FAM_TC_SPLIT),
     };
     *n = (int)(sizeof(t) / sizeof(t[0]));
     return t;
@@ -788,7 +1090,7 @@ void register_tc_variants(std::vector<Variant>& v) {
         x.info.family = t[i].family;
         x.info.s = t[i].stages;
         x.info.sr = 0;
-        x.info.B0 = 128;
+        x.info.B0 = t[i].BM;
         x.info.B1 = t[i].BN;
         x.info.tile = 0;
         x.info.regopt = 0;
@@ -813,13 +1115,16 @@ pgk_status tc_select(const pgk_machine* m, int M, int N, int K, pgk_dtype dtype,
     const TcVariant* t = tc_table(&n);
     const int fam = family_of(dtype);
     const int natural = dtype == PGK_FP8_E4M3 ? 128 : 64;
-    if (prog->B0 != 128 || (prog->tile != 0 && prog->tile != natural) || prog->s < 1) {
-        set_error("tensor-core tiles are 128 x B1 with the natural K depth (B0=%d tile=%d)", prog->B0,
-                  prog->tile);
+    if ((prog->B0 != 128 && prog->B0 != 256) || (prog->tile != 0 && prog->tile != natural) ||
+        prog->s < 1) {
+        set_error("tensor-core tiles are 128 x B1 (one CTA) or 256 x 256 (a CTA pair) with the natural "
+                  "K depth (B0=%d tile=%d)", prog->B0, prog->tile);
         return PGK_ERR_UNSUPPORTED;
     }
     for (int i = 0; i < n; ++i) {
-        if (t[i].family != fam || t[i].BN != prog->B1 || t[i].stages != prog->s) continue;
+        if (t[i].family != fam || t[i].BM != prog->B0 || t[i].BN != prog->B1 ||
+            t[i].stages != prog->s)
+            continue;
         // resource counters of the variant against the machine parameters
         if (t[i].threads > m->max_threads_per_block || t[i].smem > m->smem_per_block_optin ||
             t[i].tmem_cols > 512 || m->cc_major != 10) {
@@ -841,7 +1146,8 @@ pgk_status tc_select(const pgk_machine* m, int M, int N, int K, pgk_dtype dtype,
         *out = c;
         return PGK_OK;
     }
-    set_error("no tensor-core variant with B1=%d stages=%d for this form", prog->B1, prog->s);
+    set_error("no tensor-core variant with B0=%d B1=%d stages=%d for this form", prog->B0, prog->B1,
+              prog->s);
     return PGK_ERR_UNSUPPORTED;
 }
 
@@ -859,19 +1165,22 @@ pgk_status tc_gemm_launch(const pgk_case& c, int M, int N, int K, pgk_dtype dtyp
         return PGK_ERR_INVALID_ARG;
     }
     const int esz = dtype == PGK_FP8_E4M3 ? 1 : 2;
-    CUtensorMap ma, mb, ma2, mb2;
-    if ((st = make_map(&ma, A, M, K, lda, esz, 128)) != PGK_OK) return st;
-    if ((st = make_map(&mb, Bt, N, K, ldbt, esz, t[i].BN)) != PGK_OK) return st;
+    TcMaps maps;
+    if ((st = make_map(&maps.a, A, M, K, lda, esz, 128)) != PGK_OK) return st;
+    if ((st = make_map(&maps.b, Bt, N, K, ldbt, esz, t[i].b_box)) != PGK_OK) return st;
+    if ((st = make_map(&maps.bh, Bt, N, K, ldbt, esz, t[i].b_box / 2)) != PGK_OK) return st;
     if (dtype == PGK_SPLIT_BF16) {
         if (!A_lo || !Bt_lo) {
             set_error("split form needs the lo operands");
             return PGK_ERR_INVALID_ARG;
         }
-        if ((st = make_map(&ma2, A_lo, M, K, lda, esz, 128)) != PGK_OK) return st;
-        if ((st = make_map(&mb2, Bt_lo, N, K, ldbt, esz, t[i].BN)) != PGK_OK) return st;
+        if ((st = make_map(&maps.a2, A_lo, M, K, lda, esz, 128)) != PGK_OK) return st;
+        if ((st = make_map(&maps.b2, Bt_lo, N, K, ldbt, esz, t[i].b_box)) != PGK_OK) return st;
+        if ((st = make_map(&maps.b2h, Bt_lo, N, K, ldbt, esz, t[i].b_box / 2)) != PGK_OK) return st;
     } else {
-        ma2 = ma;
-        mb2 = mb;
+        maps.a2 = maps.a;
+        maps.b2 = maps.b;
+        maps.b2h = maps.bh;
     }
     if (dtype == PGK_FP8_E4M3 && (!sA || !sB)) {
         set_error("FP8 form needs the tile scales");
@@ -880,6 +1189,7 @@ pgk_status tc_gemm_launch(const pgk_case& c, int M, int N, int K, pgk_dtype dtyp
     pgk_machine m;
     if ((st = current_machine(&m, NULL)) != PGK_OK) return st;
     TcParams p;
+    memset(&p, 0, sizeof(p));
     p.M = M;
     p.N = N;
     p.K = K;
@@ -890,25 +1200,13 @@ pgk_status tc_gemm_launch(const pgk_case& c, int M, int N, int K, pgk_dtype dtyp
     p.sB = sB;
     p.err = device_error_word(&st);
     if (!p.err) return st;
-    const long long tiles = (long long)((M + 127) / 128) * ((N + t[i].BN - 1) / t[i].BN);
-    const int grid = (int)std::min<long long>(tiles, m.sm_count);
-    cudaError_t e = t[i].launch(ma, mb, ma2, mb2, p, grid, stream);
+    const long long tiles = (long long)((M + t[i].BM - 1) / t[i].BM) * ((N + t[i].BN - 1) / t[i].BN);
+    cudaError_t e = t[i].launch(maps, p, tiles, m.sm_count, stream);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
     return PGK_OK;
 }
 
 // ------------------------------------------------------- grouped launches
-template <class Cfg>
-static cudaError_t launch_tc_grouped(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& a2,
-                                     const CUtensorMap& b2, const TcParams& p, int grid,
-                                     cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_tc_gemm<Cfg, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<Cfg, true><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a, b, a2, b2, p);
-    return cudaGetLastError();
-}
-
 struct TcGroupedVariant {
     pgk_dtype dtype;
     int BN, stages;
@@ -918,10 +1216,10 @@ struct TcGroupedVariant {
 // 128-wide tiles only: a group of uneven problems wastes less on ragged edges
 static const TcGroupedVariant* tcg_table(int* n) {
     static const TcGroupedVariant t[] = {
-        {PGK_BF16, 128, 6, launch_tc_grouped<TcCfg<MODE_BF16, 128, 6>>},
-        {PGK_SPLIT_BF16, 128, 3, launch_tc_grouped<TcCfg<MODE_SPLIT, 128, 3>>},
-        {PGK_SPLIT_BF16, 128, 6, launch_tc_grouped<TcCfg<MODE_SPLIT3, 128, 6>>},
-        {PGK_FP8_E4M3, 128, 6, launch_tc_grouped<TcCfg<MODE_FP8, 128, 6>>},
+        {PGK_BF16, 128, 6, launch_tc<TcCfg<MODE_BF16, 128, 6>, true>},
+        {PGK_SPLIT_BF16, 128, 3, launch_tc<TcCfg<MODE_SPLIT, 128, 3>, true>},
+        {PGK_SPLIT_BF16, 128, 6, launch_tc<TcCfg<MODE_SPLIT3, 128, 6>, true>},
+        {PGK_FP8_E4M3, 128, 6, launch_tc<TcCfg<MODE_FP8, 128, 6>, true>},
     };
     *n = (int)(sizeof(t) / sizeof(t[0]));
     return t;
@@ -1085,16 +1383,18 @@ pgk_status tc_gemm_grouped(int G, const pgk_problem* pr, pgk_dtype dtype, const 
                                      (uint16_t*)b0, (uint16_t*)b1, kst, s)) != PGK_OK)
             return st;
     }
-    CUtensorMap ma, mb, ma2, mb2;
-    if ((st = make_map(&ma, a0, (int)rowsA, (int)kst, (int)kst, esz, 128)) != PGK_OK) return st;
-    if ((st = make_map(&mb, b0, (int)rowsB, (int)kst, (int)kst, esz, v->BN)) != PGK_OK) return st;
+    TcMaps maps;
+    if ((st = make_map(&maps.a, a0, (int)rowsA, (int)kst, (int)kst, esz, 128)) != PGK_OK) return st;
+    if ((st = make_map(&maps.b, b0, (int)rowsB, (int)kst, (int)kst, esz, v->BN)) != PGK_OK) return st;
     if (split) {
-        if ((st = make_map(&ma2, a1, (int)rowsA, (int)kst, (int)kst, esz, 128)) != PGK_OK) return st;
-        if ((st = make_map(&mb2, b1, (int)rowsB, (int)kst, (int)kst, esz, v->BN)) != PGK_OK) return st;
+        if ((st = make_map(&maps.a2, a1, (int)rowsA, (int)kst, (int)kst, esz, 128)) != PGK_OK) return st;
+        if ((st = make_map(&maps.b2, b1, (int)rowsB, (int)kst, (int)kst, esz, v->BN)) != PGK_OK) return st;
     } else {
-        ma2 = ma;
-        mb2 = mb;
+        maps.a2 = maps.a;
+        maps.b2 = maps.b;
     }
+    maps.bh = maps.b;     // grouped launches run whole tiles only
+    maps.b2h = maps.b2;
     TcParams p;
     memset(&p, 0, sizeof(p));
     // FP8: the scale arrays' row strides (ceil(K/128) and ceil(N/128) of a single launch)
@@ -1108,8 +1408,7 @@ pgk_status tc_gemm_grouped(int G, const pgk_problem* pr, pgk_dtype dtype, const 
     p.gtiles = reinterpret_cast<const int4*>(dt + off_t);
     p.gprobs = reinterpret_cast<const TcProb*>(dt);
     p.ntiles_g = (int)tiles;
-    const int grid = (int)std::min<long long>(tiles, m.sm_count);
-    cudaError_t e = v->launch(ma, mb, ma2, mb2, p, grid, s);
+    cudaError_t e = v->launch(maps, p, tiles, m.sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "grouped tensor-core GEMM launch");
     return PGK_OK;
 }

@@ -35,14 +35,16 @@ def _host(x, pinned):
 
 
 FORMS = [(pgk.F32, pgk.params(16, 16, 8, 8, 8)), (pgk.SPLIT_BF16, pgk.params(128, 256, 2, 0, 0)),
-         (pgk.BF16, pgk.params(128, 256, 4, 0, 0)), (pgk.FP8_E4M3, pgk.params(128, 256, 4, 0, 0))]
+         (pgk.BF16, pgk.params(128, 256, 4, 0, 0)), (pgk.FP8_E4M3, pgk.params(128, 256, 4, 0, 0)),
+         (pgk.SPLIT_BF16, pgk.params(256, 256, 3, 0, 0)), (pgk.BF16, pgk.params(256, 256, 6, 0, 0))]
 
 
 @pytest.mark.parametrize("dtype,prog", FORMS)
 @pytest.mark.parametrize("pinned_c", [True, False])
 def test_equals_device_path(dev, dtype, prog, pinned_c):
-    """Two row panels split at row 256 (a multiple of the 128-row tiles and FP8 scale
-    blocks) give the whole-matrix result bit for bit."""
+    """Two row panels split at row 256 (a multiple of the 128-row tiles, of the
+    256-row CTA-pair tiles and of the FP8 scale blocks) give the whole-matrix result
+    bit for bit."""
     M, N, K = 300, 272, 384
     A, B = inputs.gemm_operands(M, N, K, seed=3)
     Ah, Bh = _host(A, True), _host(B, True)

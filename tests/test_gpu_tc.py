@@ -11,8 +11,11 @@ from paper_1801_04348_gb300 import inputs, pgk
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = {pgk.BF16: [(256, 4), (128, 6), (256, 3), (128, 4)], pgk.SPLIT_BF16: [(128, 3), (256, 2), (256, 4), (128, 6)],
-            pgk.FP8_E4M3: [(128, 6), (256, 4)]}
+# every compiled tile program (B0, B1, stages) of each form; B0 = 256 is a CTA pair
+VARIANTS = {pgk.BF16: [(128, 256, 4), (128, 128, 6), (128, 256, 3), (128, 128, 4), (256, 256, 6)],
+            pgk.SPLIT_BF16: [(128, 128, 3), (128, 256, 2), (128, 256, 4), (128, 128, 6), (256, 256, 3),
+                             (256, 256, 6)],
+            pgk.FP8_E4M3: [(128, 128, 6), (128, 256, 4)]}
 
 
 @pytest.fixture(scope="module")
@@ -139,8 +142,8 @@ def test_integer_inputs_exact(dev, form):
         B[::128, ::128] = 7
     ref = oracle.gemm(A, B)
     ops = prep(dev, A, B, form)
-    for bn, st in VARIANTS[form]:
-        C = run_lowp(dev, form, ops, M, N, K, pgk.params(128, bn, st, 0, 0))
+    for bm, bn, st in VARIANTS[form]:
+        C = run_lowp(dev, form, ops, M, N, K, pgk.params(bm, bn, st, 0, 0))
         assert np.array_equal(C.astype(np.float64), ref), (form, bn, st)
 
 
@@ -167,12 +170,61 @@ def test_ragged_against_dequantised_oracle(dev, form, M, N, K):
     else:
         ref = oracle.gemm(Ad, Bd)
     absab = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64)
-    for bn, st in VARIANTS[form]:
-        C = run_lowp(dev, form, ops, M, N, K, pgk.params(128, bn, st, 0, 0)).astype(np.float64)
+    for bm, bn, st in VARIANTS[form]:
+        C = run_lowp(dev, form, ops, M, N, K, pgk.params(bm, bn, st, 0, 0)).astype(np.float64)
         # FP32 accumulation of K products (3K for split): gamma bound on |A||B|
         k_eff = 3 * K if form == pgk.SPLIT_BF16 else K
         bound = (k_eff + 2) * 2.0 ** -24 * absab * 2.5 + 1e-30
         assert np.all(np.abs(C - ref) <= bound), (form, bn, st)
+
+
+# (pair program, single-CTA program of the same mode and issue order)
+PAIR_TWINS = [(pgk.BF16, (256, 256, 6), (128, 256, 4)),
+              (pgk.SPLIT_BF16, (256, 256, 6), (128, 256, 4)),   # three BF16-sized passes
+              (pgk.SPLIT_BF16, (256, 256, 3), (128, 256, 2))]   # hi and lo in one stage
+
+
+@pytest.mark.parametrize("form,pair,single", PAIR_TWINS)
+@pytest.mark.parametrize("M,N,K", [(1000, 777, 1200), (256, 256, 64), (513, 1030, 3000)])
+def test_cta_pair_equals_single_cta(dev, form, pair, single, M, N, K):
+    """A CTA pair computes each 128-row half of its 256 x 256 tile with the same
+    products in the same K order as a single CTA's 128 x 256 tile, so the two
+    programs agree bit for bit, ragged edges included (rows of the second CTA
+    beyond M, columns of either half beyond N)."""
+    A, B = inputs.gemm_operands(M, N, K, seed=M + 2 * N + 5 * K, dist="normal")
+    ops = prep(dev, A, B, form)
+    Cp = run_lowp(dev, form, ops, M, N, K, pgk.params(*pair, 0, 0))
+    Cs = run_lowp(dev, form, ops, M, N, K, pgk.params(*single, 0, 0))
+    assert not np.isnan(Cp).any()
+    assert np.array_equal(Cp, Cs)
+
+
+# (form, 256-wide program, 128-wide program of the same mode, shape): on a 152-SM
+# GPU the 256-wide launch leaves a tail that fills at most half a round (172 tiles
+# on 152 SMs, 88 pair tiles on 76 SM pairs), which it runs as column halves (BF16
+# and split forms)
+TAIL_CASES = [(pgk.BF16, (128, 256, 4), (128, 128, 4), (5504, 1024, 192)),
+              (pgk.SPLIT_BF16, (128, 256, 4), (128, 128, 6), (5504, 1000, 200)),
+              (pgk.SPLIT_BF16, (256, 256, 3), (128, 128, 3), (5632, 1024, 192)),
+              (pgk.BF16, (256, 256, 6), (128, 128, 4), (5632, 1000, 200))]
+
+
+@pytest.mark.parametrize("form,wide,narrow,shape", TAIL_CASES)
+def test_tail_halves_equal_whole_tiles(dev, form, wide, narrow, shape):
+    """Tail balancing runs the last tiles of a 256-wide launch as two 128-column
+    halves; every element is still the same sequence of products, so the launch
+    equals a 128-wide program (which never splits) bit for bit, and the product
+    meets the form's tolerance against the FP64 oracle on sampled rows."""
+    M, N, K = shape
+    A, B = inputs.gemm_operands(M, N, K, seed=17, dist="normal")
+    ops = prep(dev, A, B, form)
+    Cw = run_lowp(dev, form, ops, M, N, K, pgk.params(*wide, 0, 0))
+    Cn = run_lowp(dev, form, ops, M, N, K, pgk.params(*narrow, 0, 0))
+    assert not np.isnan(Cw).any()
+    assert np.array_equal(Cw, Cn)
+    rows = np.linspace(0, M - 1, 48).astype(np.int64)
+    err = oracle.rel_frobenius(Cw[rows].astype(np.float64), oracle.gemm(A, B, rows=rows))
+    assert err <= TOL[form], err
 
 
 TOL = {pgk.BF16: 2e-2, pgk.SPLIT_BF16: 2e-5, pgk.FP8_E4M3: 5e-2}

@@ -19,9 +19,10 @@ from helpers import gamma
 pytestmark = pytest.mark.gpu
 
 SIZES = list(itertools.product(range(1, 10), repeat=3))
-TC_VARIANTS = {pgk.BF16: [(256, 4), (128, 6), (256, 3), (128, 4)],
-               pgk.SPLIT_BF16: [(128, 3), (256, 2), (256, 4), (128, 6)],
-               pgk.FP8_E4M3: [(128, 6), (256, 4)]}
+TC_VARIANTS = {pgk.BF16: [(128, 256, 4), (128, 128, 6), (128, 256, 3), (128, 128, 4), (256, 256, 6)],
+               pgk.SPLIT_BF16: [(128, 128, 3), (128, 256, 2), (128, 256, 4), (128, 128, 6),
+                                (256, 256, 3), (256, 256, 6)],
+               pgk.FP8_E4M3: [(128, 128, 6), (128, 256, 4)]}
 
 
 @pytest.fixture(scope="module")
@@ -95,11 +96,11 @@ def _tc_all(dev, A, B, form):
     ops = _prep(dev, A, B, form)
     Kp = ops["A"].stride(0)
     Cs = []
-    for bn, st in TC_VARIANTS[form]:
+    for bm, bn, st in TC_VARIANTS[form]:
         C = torch.full((M, N), float("nan"), device=dev)
         pgk.gemm_lowp(M, N, K, form, ops["A"], Kp, ops["Bt"], Kp, C, N, A_lo=ops.get("A_lo"),
                       Bt_lo=ops.get("Bt_lo"), scaleA=ops.get("scaleA"),
-                      scaleB=ops.get("scaleB"), prog=pgk.params(128, bn, st, 0, 0))
+                      scaleB=ops.get("scaleB"), prog=pgk.params(bm, bn, st, 0, 0))
         Cs.append(C)
     C = torch.full((M, N), float("nan"), device=dev)
     pgk.gemm(_t(A, dev), _t(B, dev), C, form, None)
