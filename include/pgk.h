@@ -212,8 +212,9 @@ PGK_API pgk_status pgk_gemm(int M, int N, int K, pgk_dtype dtype, const float* A
                     const pgk_params* prog, void* stream);
 
 /* GEMM on host buffers: C = A B (beta = 0) or C += A B (beta = 1) with A, B and
- * C in host memory, row-major FP32 as for pgk_gemm (dtype selects the form,
- * prog = NULL picks the tuned program).  An extension of the method for callers
+ * C in host memory, row-major FP32 as for pgk_gemm (dtype selects the form;
+ * prog = NULL takes the program the tune cache holds for M x N x K for every
+ * panel, else each panel's own tuned or selected program).  An extension of the method for callers
  * whose operands live in host memory; the paper's kernels read device memory only.
  * The library copies A and B into one of two device buffer sets that it owns,
  * on a stream of its own, then runs the GEMM on `stream`; consecutive calls

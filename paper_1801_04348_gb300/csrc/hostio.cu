@@ -196,6 +196,10 @@ pgk_status pgk_gemm_host(int M, int N, int K, pgk_dtype dtype, const float* A, i
     int sms = 0;
     PGK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     const bool tc = dtype == PGK_BF16 || dtype == PGK_SPLIT_BF16 || dtype == PGK_FP8_E4M3;
+    // without explicit parameters, the program tuned for the whole matrix (if any)
+    // plans the panels and runs all of them, as pgk_gemm would run the whole matrix
+    pgk_params tuned;
+    if (!prog && pgk_tune_cache_get(M, N, K, dtype, &tuned) == PGK_OK) prog = &tuned;
     const int bn = tc ? (prog ? prog->B1 : 256) : (prog ? std::max(1, prog->B1 * prog->s) : 128);
     const int bm = tc && prog && prog->B0 == 256 ? 256 : 128;
     int starts[9];

@@ -430,9 +430,11 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
     const uint32_t tmem_base = tmem_base_sh;
     volatile int* abort_flag = &abort_sh;
 
-    // tile t -> (tm, tn): groups of 16 tile-rows walked column by column
+    // tile t -> (tm, tn): groups of 2048 rows of tiles (16 single-CTA or 8 pair tile
+    // rows) walked column by column, so that the tiles resident at once share
+    // operand panels in L2
     auto coords = [&](int t, int& tm, int& tn) {
-        const int G = 16;
+        const int G = 16 * Cfg::BM / Cfg::TM;
         const int per = G * tiles_n;
         const int g = t / per;
         const int first = g * G;

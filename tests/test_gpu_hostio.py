@@ -127,3 +127,19 @@ def test_pageable_inputs(dev):
     pgk.gemm_host(Ah, Bh, Ch, pgk.F32, prog)
     torch.cuda.synchronize()
     assert np.array_equal(Ch.numpy(), _device_result(dev, A, B, pgk.F32, prog))
+
+
+def test_tuned_program_runs_every_panel(dev):
+    """prog = NULL with a program in the tune cache for the whole shape: the panels
+    are planned for it (256-row CTA-pair tiles here) and each runs it, so the
+    result equals pgk_gemm's on the whole matrix, which runs the same program."""
+    M, N, K = 1000, 520, 384
+    A, B = inputs.gemm_operands(M, N, K, seed=13)
+    pgk.tune_cache_put(M, N, K, pgk.SPLIT_BF16, pgk.params(256, 256, 3, 0, 0))
+    Ah, Bh = _host(A, True), _host(B, True)
+    Ch = _host(np.full((M, N), np.nan, np.float32), True)
+    pgk.gemm_host(Ah, Bh, Ch, pgk.SPLIT_BF16, None)
+    torch.cuda.synchronize()
+    ref = _device_result(dev, A, B, pgk.SPLIT_BF16, None)
+    assert np.array_equal(Ch.numpy(), ref)
+    assert np.array_equal(ref, _device_result(dev, A, B, pgk.SPLIT_BF16, pgk.params(256, 256, 3, 0, 0)))
