@@ -94,15 +94,16 @@ cudaMemoryType memory_type(const void* p) {
 }
 
 // Row panels in tile rows of bm rows (128, or 256 for CTA-pair tiles): the
-// smallest panel of at least 1/8 of the tile rows whose tile count (panel rows x
-// column tiles of width bn) is a multiple of the number of tile slots (SMs, or
-// SM pairs), repeated, the remainder last; else two halves.  Returns the number
-// of panels (<= 8) and their first rows in starts[0..n] (starts[n] = M).
+// smallest panel of at least 1/8 of the tile rows (and at most all but one) whose
+// tile count (panel rows x column tiles of width bn) is a multiple of the number
+// of tile slots (SMs, or SM pairs), repeated, the remainder last; else two halves.
+// Returns the number of panels (<= 8) and their first rows in starts[0..n]
+// (starts[n] = M).
 int plan_panels(int M, int N, int bm, int bn, int slots, int* starts) {
     const int T = (M + bm - 1) / bm, tn = (N + bn - 1) / bn;
     int r = 0;
     if (T >= 2 && slots > 0)
-        for (int c = std::max(1, (T + 7) / 8); c <= T / 2 && !r; ++c)
+        for (int c = std::max(1, (T + 7) / 8); c <= T - 1 && !r; ++c)
             if (((long long)c * tn) % slots == 0) r = c;
     if (!r) r = T >= 2 ? (T + 1) / 2 : T;
     int n = 0;

@@ -25,6 +25,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <mutex>
 #include <vector>
@@ -39,6 +40,9 @@ namespace pgk {
 enum { MODE_BF16 = 0, MODE_SPLIT = 1, MODE_FP8 = 2, MODE_SPLIT3 = 3 };
 
 static constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ULL;  // 4 s
+// drains after an abort: copies and MMAs already issued finish within microseconds;
+// a pair leader may also wait on a stage its peer never filled, so keep this short
+static constexpr unsigned long long DRAIN_LIMIT_NS = 100000000ULL;  // 100 ms
 static constexpr unsigned int ERR_TIMEOUT_PRODUCER = 0x1u;
 static constexpr unsigned int ERR_TIMEOUT_MMA = 0x2u;
 static constexpr unsigned int ERR_TIMEOUT_EPILOGUE = 0x4u;
@@ -559,7 +563,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     if (issued_mask & (1u << s)) {
                         const unsigned long long t0 = globaltimer();
                         while (!mbar_try_wait(&full_bar[s], (last_parity >> s) & 1u)) {
-                            if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                            if (globaltimer() - t0 > DRAIN_LIMIT_NS) {
                                 atomicOr(p.err, ERR_TIMEOUT_DRAIN);
                                 break;
                             }
@@ -687,7 +691,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     mma_commit(&drain_bar);
                 const unsigned long long t0 = globaltimer();
                 while (!mbar_try_wait(&drain_bar, 0)) {
-                    if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                    if (globaltimer() - t0 > DRAIN_LIMIT_NS) {
                         atomicOr(p.err, ERR_TIMEOUT_DRAIN);
                         break;
                     }
@@ -1036,10 +1040,18 @@ static cudaError_t launch_tc(const TcMaps& maps, const TcParams& p0, long long t
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
+    // resident two-CTA clusters of this variant, queried once per device
+    static std::atomic<int> resident[64];
+    int dev = 0;
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    int clusters = dev >= 0 && dev < 64 ? resident[dev].load() : 0;
+    if (clusters < 1) {
+        e = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
+        if (e != cudaSuccess) return e;
+        if (clusters < 1) return cudaErrorInvalidConfiguration;
+        if (dev >= 0 && dev < 64) resident[dev].store(clusters);
+    }
     clusters = std::min(clusters, sm_count / 2);
     if (CAN_TAIL) p.tail = tail_tiles(tiles, clusters, Cfg::BN);
     clusters = (int)std::min<long long>(tiles + p.tail, clusters);
