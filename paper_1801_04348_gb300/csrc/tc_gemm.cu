@@ -2,8 +2,10 @@
 // forms (BF16, split BF16, per-tile scaled FP8 E4M3), FP32 accumulation in
 // tensor memory.
 //
-// One persistent CTA per SM walks output tiles of BM x BN (BM = 128).  Warp
-// roles:
+// One persistent CTA per SM walks output tiles of BM x BN (BM = 128), or, for
+// the CTA-pair variants, one two-CTA cluster per SM pair walks 256 x 256 tiles
+// (each CTA stages and accumulates its 128 rows; the even CTA issues the MMAs
+// with cta_group::2).  Warp roles:
 //   warp 0  TMA producer: 128-byte-wide K slices of A (BM rows) and of B^T
 //           (BN rows) land in a STAGES-deep ring of 128B-swizzled shared tiles,
 //           completion tracked by mbarrier transaction counts;
@@ -245,6 +247,15 @@ __device__ __forceinline__ void tmem_ld_wait() {
 }
 
 // ---------------------------------------------- CTA pairs (cta_group::2)
+// Two CTAs of a cluster share one 256-row tile: each stages its own 128 rows of A
+// and its own half of the B^T rows, the even CTA (the leader) issues the MMAs,
+// which read both CTAs' shared tiles and write both CTAs' tensor memory.
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
 // First tile and tile stride of this CTA's work unit (a CTA, or a CTA pair).
 template <bool PAIR>
 __device__ __forceinline__ int tile_first() {
@@ -254,21 +265,11 @@ template <bool PAIR>
 __device__ __forceinline__ unsigned tile_stride() {
     return PAIR ? gridDim.x >> 1 : gridDim.x;
 }
-__device__ __forceinline__ uint32_t cluster_ctarank();
 // rank of this CTA in its pair (0: the leader); 0 for single-CTA tiles
 template <bool PAIR>
 __device__ __forceinline__ uint32_t pair_rank() {
     if constexpr (PAIR) return cluster_ctarank();
     return 0u;
-}
-
-// Two CTAs of a cluster share one 256-row tile: each stages its own 128 rows of A
-// and its own half of the B^T rows, the even CTA (the leader) issues the MMAs,
-// which read both CTAs' shared tiles and write both CTAs' tensor memory.
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
 }
 
 // shared::cluster address of the same shared-memory offset in CTA `rank`
