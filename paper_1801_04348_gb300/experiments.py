@@ -446,6 +446,22 @@ def peaks(dev, stream):
     n = 8192
     flops = 2.0 * n * n * n
     try:
+        # FP32 SGEMM with TF32 off: context for the SIMT fraction
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        a = torch.randn(n, n, device=dev)
+        b = torch.randn(n, n, device=dev)
+        run = lambda: torch.matmul(a, b)
+        for _ in range(3):
+            run()
+        clk = _clock_sampler()
+        ms = _events_ms(run, 8, stream)
+        out["torch_fp32_matmul"] = {"ms": ms, "tflops": flops / ms / 1e9, "sm_mhz": _clock_median(clk)}
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        del a, b
+    except Exception as e:  # context only
+        out["torch_fp32_matmul"] = {"error": str(e)[:200]}
+    try:
         a = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
         b = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
         run = lambda: torch.matmul(a, b)
