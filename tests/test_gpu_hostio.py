@@ -95,15 +95,19 @@ def test_consecutive_calls_alternate_and_grow(dev):
         assert np.array_equal(Ch.numpy(), _device_result(dev, A, B, pgk.F32, prog))
 
 
-def test_sampled_rows_at_8192(dev):
-    """The split form at 8192^3 on pinned host buffers, sampled rows against the oracle."""
+@pytest.mark.parametrize("prog", [(128, 256, 2), (256, 256, 3)])
+def test_sampled_rows_at_8192(dev, prog):
+    """The split form at 8192^3 on pinned host buffers (single-CTA tiles: four panels
+    of 19, 19, 19 and 7 tile rows; CTA pairs: 19 and 13 pair rows), rows on both sides
+    of every panel boundary against the oracle."""
     M = N = K = 8192
     A, B = inputs.gemm_operands(M, N, K, seed=0, dist="normal")
     Ah, Bh = _host(A, True), _host(B, True)
     Ch = torch.empty(M, N).pin_memory()
-    pgk.gemm_host(Ah, Bh, Ch, pgk.SPLIT_BF16, pgk.params(128, 256, 2, 0, 0))
+    pgk.gemm_host(Ah, Bh, Ch, pgk.SPLIT_BF16, pgk.params(*prog, 0, 0))
     torch.cuda.synchronize()
-    rows = np.linspace(0, M - 1, 16).astype(np.int64)
+    edges = [2431, 2432, 4863, 4864, 7295, 7296]
+    rows = np.unique(np.concatenate([np.linspace(0, M - 1, 16).astype(np.int64), edges]))
     err = oracle.rel_frobenius(Ch.numpy()[rows].astype(np.float64), oracle.gemm(A, B, rows=rows))
     assert err <= 2e-5, err
 
