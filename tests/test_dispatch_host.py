@@ -101,3 +101,38 @@ def test_real_gb300_like_machine_picks_4a3a(built):
                     assert st == 0 and c.leaf == pgk.LEAF_4A3A and c.params.tile == b0
                 else:
                     assert st == 2
+
+
+def test_tensor_core_case_selection(built):
+    """Tensor-core programs (host code): every default candidate of each form,
+    CTA-pair programs (B0 = 256) included, selects its variant on a GB300-like
+    machine; programs without a compiled variant are UNSUPPORTED, and a machine
+    whose opt-in shared memory or compute capability does not fit makes a variant
+    INFEASIBLE (its resource counters against the machine parameters)."""
+    m = pgk.Machine(1024, 49152, 232448, 65536, 65536, 255, 2048, 152, 32, 10, 3, 0)
+    for form in (pgk.BF16, pgk.SPLIT_BF16, pgk.FP8_E4M3):
+        cands = pgk.default_candidates(form)
+        assert cands
+        for p in cands:
+            st, c = pgk.select_case(m, 8192, 8192, 8192, form, p, raise_on_error=False)
+            assert st == 0, (form, p.as_tuple(), pgk.last_error())
+            assert (c.params.B0, c.params.B1, c.params.s) == (p.B0, p.B1, p.s)
+            assert c.smem_bytes <= m.smem_per_block_optin and c.threads <= m.max_threads_per_block
+        for bad in [(256, 128, 3), (512, 256, 3), (128, 192, 4)]:
+            st, _ = pgk.select_case(m, 8192, 8192, 8192, form, pgk.params(*bad, 0, 0),
+                                    raise_on_error=False)
+            assert st == 3, (form, bad)
+    # CTA pairs exist for the kind::f16 forms only
+    assert any(p.B0 == 256 for p in pgk.default_candidates(pgk.SPLIT_BF16))
+    assert any(p.B0 == 256 for p in pgk.default_candidates(pgk.BF16))
+    st, _ = pgk.select_case(m, 8192, 8192, 8192, pgk.FP8_E4M3, pgk.params(256, 256, 6, 0, 0),
+                            raise_on_error=False)
+    assert st == 3
+    small = pgk.Machine(1024, 49152, 200000, 65536, 65536, 255, 2048, 152, 32, 10, 3, 0)
+    st, _ = pgk.select_case(small, 8192, 8192, 8192, pgk.SPLIT_BF16, pgk.params(256, 256, 3, 0, 0),
+                            raise_on_error=False)
+    assert st == 2
+    hopper = pgk.Machine(1024, 49152, 232448, 65536, 65536, 255, 2048, 132, 32, 9, 0, 0)
+    st, _ = pgk.select_case(hopper, 8192, 8192, 8192, pgk.BF16, pgk.params(128, 256, 4, 0, 0),
+                            raise_on_error=False)
+    assert st == 2
