@@ -1,14 +1,24 @@
 """Benchmark of the parametric GEMM hot path on GB300.
 
 One step = one GEMM C = A*B at M = N = K = 8192 (FP32 inputs, FP32 output) in
-the chosen arithmetic form, with every stage of the path inside the step:
-operand preparation (for the tensor-core forms) and the GEMM kernel; the case
-discussion runs on the host before each launch.  Inputs (256 MiB each) exceed
-the 129 MB L2, so no flush is needed between steps.
+the chosen arithmetic form (default: split BF16, three BF16 products with FP32
+accumulation, FP32-level accuracy), with every stage of the path inside the
+step: operand preparation (for the tensor-core forms) and the GEMM kernel; the
+case discussion runs on the host before each launch.  Inputs (256 MiB each)
+exceed the 129 MB L2, so no flush is needed between steps.
+
+The metric compares the chosen form with the plain FP32 parametric GEMM tuned
+exhaustively over its register-blocked variants: both arms are autotuned and
+timed on the same operands in the same run, and both report their relative
+Frobenius error and largest per-row relative error on 64 rows against the FP64
+oracle.  If the chosen form misses its tolerance the headline is the FP32 arm.
 
 Prints ONE JSON line (rank 0).  `value` is whole-job TFLOP/s (2 M N K per GEMM,
-all ranks), `roofline` describes the dominant kernel (the GEMM), `cpu_baseline`
-the FP64 CPU oracle on a bounded sample of rows of the same product.
+all ranks), `roofline` describes the dominant kernel (the GEMM),
+`config.fp32_tuned` the FP32 arm (with its own roofline against the SIMT peak),
+`cpu_baseline` the FP64 CPU oracle on a bounded sample of rows of the same
+product.  The oracle runs only in that leg (`oracle_leg`), which also yields the
+reference rows of the error columns.
 
 --impl reference times the oracle itself (the CPU reference arm) on the same
 workload, a bounded sample of rows per step.
@@ -35,7 +45,10 @@ FORM_NAMES = {"f32": "FP32 SIMT (register-blocked parametric kernel)",
               "split": "split-BF16 (3 BF16 products, tcgen05, FP32 accumulate)",
               "bf16": "BF16 tcgen05, FP32 accumulate",
               "fp8": "FP8-E4M3 per-128x128-tile scaled tcgen05, FP32 accumulate"}
-FORM_DTYPE = {"f32": "f32", "split": "bf16", "bf16": "bf16", "fp8": "fp8-e4m3"}
+# the arithmetic each form computes in: split = three BF16 products (hi*hi, hi*lo,
+# lo*hi) accumulated in FP32, FP32-level accuracy
+FORM_DTYPE = {"f32": "f32", "split": "bf16x3-split (fp32 accumulate)",
+              "bf16": "bf16 (fp32 accumulate)", "fp8": "fp8-e4m3 (fp32 accumulate)"}
 FORM_TOL = {"f32": 1e-5, "split": 2e-5, "bf16": 2e-2, "fp8": 5e-2}
 
 
@@ -112,14 +125,19 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_baseline(M, N, K, seed, target_s=12.0):
-    """Time the FP64 oracle on a bounded sample of full output rows."""
+def oracle_leg(A, B, err_rows, timed, target_s=12.0):
+    """The CPU-oracle leg: the FP64 oracle's rows `err_rows` of A*B (the reference
+    for the error columns) and, when `timed`, the oracle timed on a bounded sample
+    of full output rows (the cpu_baseline)."""
     import numpy as np
 
     import oracle
-    from paper_1801_04348_gb300 import inputs
-    A, B = inputs.gemm_operands(M, N, K, seed=seed)
     oracle.build()
+    ref = oracle.gemm(A, B, rows=err_rows)
+    if not timed:
+        return ref, None
+    M, K = A.shape
+    N = B.shape[1]
     cores = oracle.max_threads()
     # calibrate with one row per core (the oracle parallelises over rows)
     rows = np.linspace(0, M - 1, cores).astype(np.int64)
@@ -133,9 +151,9 @@ def cpu_baseline(M, N, K, seed, target_s=12.0):
     oracle.gemm(A, B, rows=rows)
     dt = time.perf_counter() - t0
     flops = 2.0 * nrows * N * K
-    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nrows} of {M} output rows of the {M}x{N}x{K} product in FP64 "
-                      f"(i-k-j loop, OpenMP), {dt:.1f} s"}
+    return ref, {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                 "sample": f"{nrows} of {M} output rows of the {M}x{N}x{K} product in FP64 "
+                           f"(i-k-j loop, OpenMP), {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -179,6 +197,52 @@ def run_reference(args):
     return 0
 
 
+def row_errors(got, ref):
+    """(relative Frobenius error, largest per-row relative error) of sampled rows."""
+    import numpy as np
+    got = np.asarray(got, dtype=np.float64)
+    d = np.linalg.norm(got - ref, axis=1)
+    r = np.linalg.norm(ref, axis=1)
+    frob = float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+    return frob, float(np.max(d / np.maximum(r, 1e-300)))
+
+
+def time_arm(step, gemm_events, steps, warmup, stream, dev, ws, local):
+    """W untimed steps, ~0.6 s of untimed steps while the clock sampler starts, then
+    `steps` steps between a barrier and a synchronise, timed with CUDA events on
+    the launching stream.  Returns (ms, per-GEMM ms list, clocks)."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize(dev)
+    # nvidia-smi needs a moment to start: keep the GPU busy with extra untimed
+    # steps for ~0.6 s after starting it, so the samples see the kernel under load
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_busy = time.perf_counter()
+    with torch.cuda.stream(stream):
+        while time.perf_counter() - t_busy < 0.6:
+            step()
+            torch.cuda.synchronize(dev)
+    gemm_events.clear()
+    if ws > 1:
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    gemm_ms = [a.elapsed_time(b) for a, b in gemm_events[-steps:]] if gemm_events else []
+    return ms, gemm_ms, clocks
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,13 +250,17 @@ def main():
                     help="timed steps (0 = as many as fill about 3 s)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="auto", choices=["auto", "f32", "split", "bf16", "fp8"])
+    ap.add_argument("--form", default="split", choices=["split", "f32", "bf16", "fp8"],
+                    help="the chosen arithmetic form (the headline); the tuned FP32 arm is "
+                         "measured beside it")
     ap.add_argument("--size", type=int, default=8192)
     ap.add_argument("--shape", default=None,
                     help="M,N,K of the GEMM (default: --size for all three); other shapes than "
                          "8192^3 are measurements beside the benchmark workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32-arm", action="store_true",
+                    help="skip the tuned FP32 arm (the comparison the metric names)")
     ap.add_argument("--tune-log", default=None, help="append the autotuner's CSV rows here")
     ap.add_argument("--params", default=None,
                     help="B0,B1,s,sr,tile: use these program parameters instead of autotuning")
@@ -223,22 +291,12 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
     machine = pgk.machine_query(local)
+    err_rows = np.linspace(0, M - 1, 64).astype(np.int64)
+    err_rows_d = torch.from_numpy(err_rows).to(dev)
 
-    forms = [args.form] if args.form != "auto" else ["split", "f32"]
-    form, prog, err = None, None, None
-    for f in forms:
-        try:
-            fixed = pgk.params(*[int(x) for x in args.params.split(",")]) if args.params else None
-            prog, err = prepare_form(f, Ad, Bd, C, A, B, stream, pgk, torch, np, fixed,
-                                     args.tune_log)
-            if err <= FORM_TOL[f]:
-                form = f
-                break
-        except pgk.PgkError:
-            continue
-    if form is None:
-        raise SystemExit("no arithmetic form met its tolerance")
-
+    form = args.form
+    fixed = pgk.params(*[int(x) for x in args.params.split(",")]) if args.params else None
+    prog = tune_form(form, Ad, Bd, C, stream, pgk, torch, fixed, args.tune_log)
     step, gemm_events, launches_per_step, alg = make_step(form, prog, Ad, Bd, C, M, N, K, sh, pgk,
                                                           torch, dev)
     if args.steps <= 0:
@@ -250,66 +308,84 @@ def main():
             torch.cuda.synchronize(dev)
             dt = time.perf_counter() - t0
         args.steps = int(min(2000, max(10, 3.0 / max(dt, 1e-6))))
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-    torch.cuda.synchronize(dev)
-    # nvidia-smi needs a moment to start: keep the GPU busy with extra untimed
-    # steps for ~0.6 s after starting it, so the samples see the kernel under load
-    sampler = ClockSampler(local)
-    sampler.start()
-    t_busy = time.perf_counter()
-    with torch.cuda.stream(stream):
-        while time.perf_counter() - t_busy < 0.6:
-            step()
-            torch.cuda.synchronize(dev)
-    gemm_events.clear()
-    if ws > 1:
-        torch.distributed.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-    torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    gemm_ms = [a.elapsed_time(b) for a, b in gemm_events[-args.steps:]] if gemm_events else []
+    ms, gemm_ms, clocks = time_arm(step, gemm_events, args.steps, args.warmup, stream, dev, ws, local)
+    got_form = C[err_rows_d].cpu().numpy()
     t_max = max_over_ranks(ms / 1e3, dev, ws)
     value = whole_job_tflops(2.0 * M * N * K * args.steps, t_max, ws)
+
+    pk, pk_src = peaks()
+    roof = roofline(form, alg, gemm_ms, ms / args.steps, machine, pk, pk_src, clocks,
+                    recorded_traffic(form, prog, (M, N, K)), timed_s=ms / 1e3)
+
+    # the comparison the metric names: plain FP32 SIMT, exhaustively tuned over the
+    # register-blocked family, on the same operands
+    arm32 = None
+    if form != "f32" and not args.no_fp32_arm:
+        C32 = torch.empty(M, N, device=dev)
+        prog32 = tune_form("f32", Ad, Bd, C32, stream, pgk, torch, None, args.tune_log)
+        step32, ev32, l32, alg32 = make_step("f32", prog32, Ad, Bd, C32, M, N, K, sh, pgk, torch,
+                                             dev)
+        steps32 = max(10, min(args.steps, 40))
+        ms32, gms32, clocks32 = time_arm(step32, ev32, steps32, args.warmup, stream, dev, ws, local)
+        t32 = max_over_ranks(ms32 / 1e3, dev, ws)
+        roof32 = roofline("f32", alg32, gms32, ms32 / steps32, machine, pk, pk_src, clocks32,
+                          recorded_traffic("f32", prog32, (M, N, K)), timed_s=ms32 / 1e3)
+        arm32 = {"value": whole_job_tflops(2.0 * M * N * K * steps32, t32, ws), "unit": "TFLOP/s",
+                 "ms_per_step": t32 * 1e3 / steps32, "steps": steps32,
+                 "program_params": list(prog32.as_tuple()), "roofline": roof32,
+                 "gpu_launches": l32 * steps32, "clocks": clocks32,
+                 "got": C32[err_rows_d].cpu().numpy()}
+        del C32
 
     # end to end: host (pinned) inputs -> device -> GEMM -> host result
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(form, prog, A, B, M, N, K, dev, stream, pgk, torch, args, ws)
 
-    pk, pk_src = peaks()
-    roof = roofline(form, alg, gemm_ms, ms / args.steps, machine, pk, pk_src, clocks,
-                    recorded_traffic(form, prog, (M, N, K)), timed_s=ms / 1e3)
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(M, N, K, seed=0)
+    errs = None
+    if rank == 0:
+        ref, cpu = oracle_leg(A, B, err_rows, timed=(ws == 1 and not args.no_cpu_baseline))
+        errs = {"form": row_errors(got_form, ref)}
+        if arm32 is not None:
+            errs["f32"] = row_errors(arm32.pop("got"), ref)
+    elif arm32 is not None:
+        arm32.pop("got")
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     if rank != 0:
         return 0
+    err, err_row = errs["form"]
+    met = err <= FORM_TOL[form]
+    config = {"workload": f"{M}x{N}x{K} GEMM, FP32 in/out, uniform[-1,1] seed 0(+rank), "
+                          f"form: {FORM_NAMES[form]}",
+              "M": M, "N": N, "K": K, "form": form, "program_params": list(prog.as_tuple()),
+              "rel_frobenius_err": err, "max_row_rel_err": err_row,
+              "err_sample": f"{len(err_rows)} rows against the FP64 oracle",
+              "tolerance": FORM_TOL[form], "tolerance_met": met,
+              "l2": "inputs 256 MiB each > 129 MB L2; no flush"}
     line = {
         "metric": METRIC,
         "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPE[form], "data": "synthetic",
-        "config": {"workload": f"{M}x{N}x{K} GEMM, FP32 in/out, uniform[-1,1] seed 0(+rank), "
-                               f"form: {FORM_NAMES[form]}",
-                   "M": M, "N": N, "K": K, "form": form, "program_params": list(prog.as_tuple()),
-                   "rel_frobenius_err": err, "tolerance": FORM_TOL[form],
-                   "l2": "inputs 256 MiB each > 129 MB L2; no flush"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
     }
+    if arm32 is not None:
+        e32, r32 = errs["f32"]
+        arm32.update({"rel_frobenius_err": e32, "max_row_rel_err": r32, "tolerance": FORM_TOL["f32"],
+                      "tolerance_met": e32 <= FORM_TOL["f32"]})
+        config["fp32_tuned"] = arm32
+        line["speedup_vs_fp32_tuned"] = value / arm32["value"]
+    if not met:
+        # the chosen form missed its accuracy: the headline is the tuned FP32 arm
+        line["chosen_form_missed_tolerance"] = True
+        if arm32 is not None:
+            line["value"] = arm32["value"]
+            line["ms_per_step"] = arm32["ms_per_step"]
+            line["dtype"] = FORM_DTYPE["f32"]
     print(json.dumps(line), flush=True)
     return 0
 
@@ -332,28 +408,21 @@ def whole_job_tflops(flops_per_rank, t_max, ws):
     return flops_per_rank * ws / t_max / 1e12
 
 
-def prepare_form(form, Ad, Bd, C, A, B, stream, pgk, torch, np, fixed=None, tune_log=None):
-    """Autotune the form's program parameters on the real operands and measure
-    its relative Frobenius error on 64 sampled rows against the FP64 oracle."""
-    import oracle
+def tune_form(form, Ad, Bd, C, stream, pgk, torch, fixed=None, tune_log=None):
+    """Program parameters of the form for this shape: `fixed`, else the autotuner's
+    fastest candidate on the real operands (FP32: the register-blocked family)."""
     dt = {"f32": pgk.F32, "split": pgk.SPLIT_BF16, "bf16": pgk.BF16, "fp8": pgk.FP8_E4M3}[form]
+    if fixed is not None:
+        return fixed
+    if form == "f32":
+        cands = [p for p in pgk.default_candidates(dt) if p.sr > 1]
+    else:
+        cands = pgk.default_candidates(dt)
     with torch.cuda.stream(stream):
-        if form == "f32":
-            cands = [p for p in pgk.default_candidates(dt) if p.sr > 1]
-        else:
-            cands = pgk.default_candidates(dt)
-        if fixed is not None:
-            best = fixed
-        else:
-            best, _ = pgk.autotune(Ad, Bd, C, dt, candidates=cands, reps=2, stream=stream,
-                                   log_path=tune_log)
-        pgk.gemm(Ad, Bd, C, dt, best, stream=stream)
+        best, _ = pgk.autotune(Ad, Bd, C, dt, candidates=cands, reps=2, stream=stream,
+                               log_path=tune_log)
     torch.cuda.synchronize()
-    M = A.shape[0]
-    rows = np.linspace(0, M - 1, 64).astype(np.int64)
-    ref = oracle.gemm(A, B, rows=rows)
-    got = C[torch.from_numpy(rows).to(C.device)].cpu().numpy()
-    return best, oracle.rel_frobenius(got, ref)
+    return best
 
 
 def make_step(form, prog, Ad, Bd, C, M, N, K, sh, pgk, torch, dev):

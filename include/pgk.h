@@ -19,6 +19,13 @@
  *    buffers, scheduler tables, error words) and frees them in pgk_shutdown().
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    GEMM and preparation calls are asynchronous on that stream.
+ *  - Device memory is per device: a call runs on the calling thread's current
+ *    device and uses only that device's workspaces and error word.  Calls that
+ *    use library workspaces (pgk_gemm and pgk_gemm_host in the tensor-core
+ *    forms or with split K, pgk_gemm_grouped, pgk_relerr, pgk_mlp_loss_grad)
+ *    share one set per device, so such calls on one device must not overlap on
+ *    different streams: issue them on one stream, or order the streams with
+ *    events.  Workspaces grow on demand; a growth synchronises the device.
  *  - No call aborts, traps or prints.  Every failure is returned as a
  *    pgk_status; pgk_last_error() gives a message for the calling thread.
  *  - Sizes are int; M, N, K >= 1 (zero sizes return PGK_ERR_INVALID_ARG).
@@ -393,10 +400,11 @@ PGK_API pgk_status pgk_mlp_loss_grad(int n, const int* idx, const float* X, cons
 
 /* Same result as pgk_mlp_loss_grad, but the call allocates no memory: no
  * cudaMalloc, cudaFree or allocating library routine.  This serves callers
- * that cannot allocate device memory where they need a gradient (work being
- * captured into a CUDA graph, real-time loops that forbid allocation after
- * start-up, hosts whose device memory belongs to their own pool).  The paper
- * has no counterpart to this entry point.  The per-tile partial gradients live
+ * that cannot allocate device memory where they need a gradient: real-time
+ * training loops that forbid allocation after start-up (an allocation can
+ * synchronise the device and stall the loop for milliseconds), and host
+ * applications whose device memory belongs to their own pool allocator.  The
+ * paper has no counterpart to this entry point.  The per-tile partial gradients live
  * in one static device array of PGK_MLP_NOALLOC_MAX_SAMPLES / 16 tiles
  * (about 2.4 MB), which every GPU that loads the library holds until the
  * process exits.  The first call on a device looks up that array's device

@@ -94,6 +94,7 @@ static const GroupedVariant* grouped_table(int* n) {
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     void* table = nullptr;   // GProb[G] then prefix[G+1] then counter
+    int device = 0;          // the graph and its table belong to this device
 };
 
 static std::mutex g_gmu;
@@ -101,12 +102,18 @@ static std::map<std::vector<long long>, GraphEntry> g_graphs;
 
 void grouped_release() {
     std::lock_guard<std::mutex> lk(g_gmu);
-    if (!g_graphs.empty()) cudaDeviceSynchronize();
+    if (g_graphs.empty()) return;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) cur = -1;
     for (auto& kv : g_graphs) {
+        // a replay may still be running on the graph's device
+        if (cudaSetDevice(kv.second.device) == cudaSuccess) cudaDeviceSynchronize();
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (kv.second.table) cudaFree(kv.second.table);
     }
     g_graphs.clear();
+    if (cur >= 0) cudaSetDevice(cur);
+    cudaGetLastError();
 }
 
 static bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -262,9 +269,12 @@ extern "C" pgk_status pgk_gemm_grouped(int G, const pgk_problem* problems, pgk_d
                      "table upload");
         return enqueue(*v, dt, G, total, grid, s);
     }
-    // key: the problem set (sizes, pointers), the variant and beta
+    // key: the device, the problem set (sizes, pointers), the variant and beta
+    int dev = 0;
+    PGK_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
     std::vector<long long> key;
-    key.reserve(9 * (size_t)G + 8);
+    key.reserve(9 * (size_t)G + 9);
+    key.push_back(dev);
     key.push_back(G);
     key.push_back(p.B0);
     key.push_back(p.B1);
@@ -288,6 +298,7 @@ extern "C" pgk_status pgk_gemm_grouped(int G, const pgk_problem* problems, pgk_d
     auto it = g_graphs.find(key);
     if (it == g_graphs.end()) {
         GraphEntry ge;
+        ge.device = dev;
         PGK_CUDA_TRY(cudaMalloc(&ge.table, bytes), "graph table allocation");
         cudaError_t e = cudaMemcpy(ge.table, img.data(), bytes - 16, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {

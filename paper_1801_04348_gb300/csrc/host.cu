@@ -543,6 +543,7 @@ pgk_status pgk_shutdown(void) {
     grouped_release();
     hostio_release();
     tune_cache_release();
+    noalloc_release();
     free_workspaces();
     return PGK_OK;
 }

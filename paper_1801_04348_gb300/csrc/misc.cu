@@ -17,25 +17,47 @@ namespace pgk {
 pgk_params default_params(int M, int N, int K, pgk_dtype dtype);
 
 // -------------------------------------------------------------- workspaces
+// One set of workspaces and one error word per device: a call on device d only
+// ever receives memory of device d (the current device of the calling thread).
+static constexpr int MAX_DEVICES = 64;
 static std::mutex g_ws_mu;
-static void* g_ws_ptr[WS_COUNT];
-static size_t g_ws_size[WS_COUNT];
-static unsigned int* g_err_word = nullptr;
+static void* g_ws_ptr[MAX_DEVICES][WS_COUNT];
+static size_t g_ws_size[MAX_DEVICES][WS_COUNT];
+static unsigned int* g_err_word[MAX_DEVICES];
+
+static bool current_device(int* dev, pgk_status* st) {
+    cudaError_t e = cudaGetDevice(dev);
+    if (e != cudaSuccess) {
+        *st = cuda_fail(e, "cudaGetDevice");
+        return false;
+    }
+    if (*dev < 0 || *dev >= MAX_DEVICES) {
+        set_error("device index %d out of range", *dev);
+        *st = PGK_ERR_INVALID_ARG;
+        return false;
+    }
+    return true;
+}
 
 void* workspace(int slot, size_t bytes, pgk_status* st) {
-    std::lock_guard<std::mutex> lk(g_ws_mu);
     *st = PGK_OK;
     if (slot < 0 || slot >= WS_COUNT) {
         *st = PGK_ERR_INVALID_ARG;
         return nullptr;
     }
+    int dev = 0;
+    if (!current_device(&dev, st)) return nullptr;
+    std::lock_guard<std::mutex> lk(g_ws_mu);
     if (bytes == 0) bytes = 16;
-    if (g_ws_size[slot] < bytes) {
-        if (g_ws_ptr[slot]) {
+    void*& ptr = g_ws_ptr[dev][slot];
+    size_t& size = g_ws_size[dev][slot];
+    if (size < bytes) {
+        if (ptr) {
+            // earlier work of this device may still use the old buffer
             cudaDeviceSynchronize();
-            cudaFree(g_ws_ptr[slot]);
-            g_ws_ptr[slot] = nullptr;
-            g_ws_size[slot] = 0;
+            cudaFree(ptr);
+            ptr = nullptr;
+            size = 0;
         }
         // grow geometrically so that alternating sizes do not reallocate
         size_t want = bytes + bytes / 4;
@@ -47,39 +69,54 @@ void* workspace(int slot, size_t bytes, pgk_status* st) {
             *st = PGK_ERR_NO_MEMORY;
             return nullptr;
         }
-        g_ws_ptr[slot] = p;
-        g_ws_size[slot] = want;
+        ptr = p;
+        size = want;
     }
-    return g_ws_ptr[slot];
+    return ptr;
 }
 
 unsigned int* device_error_word(pgk_status* st) {
-    std::lock_guard<std::mutex> lk(g_ws_mu);
     *st = PGK_OK;
-    if (!g_err_word) {
-        cudaError_t e = cudaMalloc(&g_err_word, sizeof(unsigned int));
-        if (e == cudaSuccess) e = cudaMemset(g_err_word, 0, sizeof(unsigned int));
+    int dev = 0;
+    if (!current_device(&dev, st)) return nullptr;
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    if (!g_err_word[dev]) {
+        unsigned int* w = nullptr;
+        cudaError_t e = cudaMalloc(&w, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemset(w, 0, sizeof(unsigned int));
         if (e != cudaSuccess) {
-            g_err_word = nullptr;
+            if (w) cudaFree(w);
             *st = cuda_fail(e, "error word allocation");
             return nullptr;
         }
+        g_err_word[dev] = w;
     }
-    return g_err_word;
+    return g_err_word[dev];
 }
 
 void free_workspaces() {
     std::lock_guard<std::mutex> lk(g_ws_mu);
-    bool any = g_err_word != nullptr;
-    for (int i = 0; i < WS_COUNT; ++i) any = any || g_ws_ptr[i] != nullptr;
-    if (any) cudaDeviceSynchronize();
-    for (int i = 0; i < WS_COUNT; ++i) {
-        if (g_ws_ptr[i]) cudaFree(g_ws_ptr[i]);
-        g_ws_ptr[i] = nullptr;
-        g_ws_size[i] = 0;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        cur = -1;
     }
-    if (g_err_word) cudaFree(g_err_word);
-    g_err_word = nullptr;
+    for (int d = 0; d < MAX_DEVICES; ++d) {
+        bool any = g_err_word[d] != nullptr;
+        for (int i = 0; i < WS_COUNT; ++i) any = any || g_ws_ptr[d][i] != nullptr;
+        if (!any) continue;
+        // work still queued on that device may use its buffers
+        if (cudaSetDevice(d) == cudaSuccess) cudaDeviceSynchronize();
+        for (int i = 0; i < WS_COUNT; ++i) {
+            if (g_ws_ptr[d][i]) cudaFree(g_ws_ptr[d][i]);
+            g_ws_ptr[d][i] = nullptr;
+            g_ws_size[d][i] = 0;
+        }
+        if (g_err_word[d]) cudaFree(g_err_word[d]);
+        g_err_word[d] = nullptr;
+    }
+    if (cur >= 0) cudaSetDevice(cur);
+    cudaGetLastError();
 }
 
 // ------------------------------------------------------------ tuning cache

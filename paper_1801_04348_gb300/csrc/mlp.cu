@@ -253,9 +253,9 @@ pgk_status pgk_mlp_adam(int count, float* theta, const float* grad, float* m, fl
 
 // ------------------------------------------------ allocation-free gradient
 // Some callers cannot allocate device memory at the point where they need a
-// gradient: code that runs while a CUDA graph is being captured, real-time or
-// embedded loops that forbid allocation after start-up, and hosts whose memory
-// is owned by their own pool allocator.  For them the per-tile partials live
+// gradient: real-time or embedded training loops that forbid allocation after
+// start-up (a cudaMalloc can synchronise the device and take milliseconds), and
+// host applications whose device memory is owned by their own pool allocator.  For them the per-tile partials live
 // in a file-scope device array sized for PGK_MLP_NOALLOC_MAX_SAMPLES samples.
 // Every GPU that loads the library holds this array until the process exits.
 namespace pgk {
@@ -285,6 +285,13 @@ static pgk_status noalloc_scratch(float** out) {
     *out = g_noalloc_ptr[dev];
     return PGK_OK;
 }
+
+// pgk_shutdown forgets the cached addresses, so that the next call looks them up
+// again (after a device reset the array may sit at another address)
+void noalloc_release() {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    for (int d = 0; d < 64; ++d) g_noalloc_ptr[d] = nullptr;
+}
 }  // namespace pgk
 
 extern "C" pgk_status pgk_mlp_loss_grad_noalloc(int n, const int* idx, const float* X,
@@ -296,7 +303,8 @@ extern "C" pgk_status pgk_mlp_loss_grad_noalloc(int n, const int* idx, const flo
     }
     if (n > PGK_MLP_NOALLOC_MAX_SAMPLES) {
         set_error("pgk_mlp_loss_grad_noalloc: %d samples exceed the static scratch limit of %d "
-                  "(use pgk_mlp_loss_grad or split the batch)", n, PGK_MLP_NOALLOC_MAX_SAMPLES);
+                  "(split the batch, or use pgk_mlp_loss_grad, which takes up to 65536)",
+                  n, PGK_MLP_NOALLOC_MAX_SAMPLES);
         return PGK_ERR_INVALID_ARG;
     }
     float* partial = nullptr;

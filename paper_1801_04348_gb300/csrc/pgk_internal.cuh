@@ -126,6 +126,8 @@ pgk_status gemm_device(int M, int N, int K, pgk_dtype dtype, const float* A, int
                        bool reuse_b);
 void tune_cache_release();
 void costmodel_release();
+// Forgets the cached device addresses of the allocation-free gradient's scratch (mlp.cu).
+void noalloc_release();
 // Learned selection for pgk_gemm(prog = NULL) on a tuning-cache miss (misc.cu).
 pgk_status learned_select(int M, int N, int K, pgk_dtype dtype, const float* A, int lda,
                           const float* B, int ldb, float* C, int ldc, int beta,

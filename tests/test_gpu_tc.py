@@ -247,11 +247,23 @@ def test_fp32_inputs_tolerance_and_beta(dev, form):
     assert err <= TOL[form], err
 
 
+def _row_rel(got, ref):
+    """Relative error of every sampled row, ||C_i - Cref_i|| / ||Cref_i||."""
+    return np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+
+
 @pytest.mark.parametrize("dist", ["normal", "normal_rowscaled"])
 @pytest.mark.parametrize("form", [pgk.BF16, pgk.SPLIT_BF16, pgk.FP8_E4M3])
 def test_full_size_8192_sampled_rows(dev, form, dist):
-    """M = N = K = 8192 (the precision workload), normal(0,1) and row-scaled
-    inputs; 32 sampled rows against the FP64 oracle; the error is printed."""
+    """M = N = K = 8192 (the precision workload), normal(0,1) inputs and the
+    set scaled by 10^uniform(-3,3) per row of A and per row of B; 32 sampled
+    rows against the FP64 oracle.  Every form meets its relative Frobenius
+    tolerance on both sets.  BF16 and split also keep every sampled row within
+    that tolerance.  FP8 does not, by its definition: one scale covers 128 rows,
+    so a row far below its tile's largest entry quantises to few or no nonzero
+    codes (its error approaches 1); against the FP64 product of the quantised
+    operands every row is then exact to FP32 accumulation, which pins the
+    per-row loss on the quantisation, not on the kernel."""
     M = N = K = 8192
     A, B = inputs.gemm_operands(M, N, K, seed=0, dist=dist)
     At, Bt = _t(A, dev), _t(B, dev)
@@ -261,7 +273,19 @@ def test_full_size_8192_sampled_rows(dev, form, dist):
     pgk.check_device_error()
     rows = np.linspace(0, M - 1, 32).astype(np.int64)
     ref = oracle.gemm(A, B, rows=rows)
-    err = oracle.rel_frobenius(C[torch.from_numpy(rows).to(dev)].cpu().numpy(), ref)
-    print(f"form={form} dist={dist} rel_frobenius={err:.3e}")
-    if dist == "normal":
-        assert err <= TOL[form], err
+    got = C[torch.from_numpy(rows).to(dev)].cpu().numpy().astype(np.float64)
+    err = oracle.rel_frobenius(got, ref)
+    row_max = float(_row_rel(got, ref).max())
+    print(f"form={form} dist={dist} rel_frobenius={err:.3e} max_row_rel={row_max:.3e}")
+    assert err <= TOL[form], err
+    if form != pgk.FP8_E4M3:
+        assert row_max <= TOL[form], row_max
+        return
+    ca, sa = quant.fp8_tile_quant(A)
+    cb, sb = quant.fp8_tile_quant(B)
+    Ad, Bd = quant.fp8_dequant(ca, sa), quant.fp8_dequant(cb, sb)
+    del ca, cb
+    refq = oracle.gemm(Ad, Bd, rows=rows)
+    absab = np.abs(Ad[rows]) @ np.abs(Bd)
+    bound = (K + 2) * 2.0 ** -24 * absab * 2.5 + 1e-30
+    assert np.all(np.abs(got - refq) <= bound)
