@@ -267,10 +267,11 @@ PGK_API pgk_status pgk_gemm_case(const pgk_case* c, int M, int N, int K, const f
  * (NULL = tuned/default).  use_graph = 1 captures the counter reset and the
  * launch in a CUDA graph, cached per problem set and replayed on later calls
  * with the same problems.
- * PGK_BF16 / PGK_SPLIT_BF16 / PGK_FP8_E4M3: three launches on `stream`: one
- * converts (FP8: quantises, 128 x 128 tile scales) every A_g, one every B_g
- * (transposed), into library workspaces packed problem after problem (each at a
- * multiple of 128 rows, K zero-padded to the K block, 64 or 128 for FP8), and one
+ * PGK_BF16 / PGK_SPLIT_BF16 / PGK_FP8_E4M3: the operands are converted into
+ * library workspaces packed problem after problem (each at a multiple of 128
+ * rows, K zero-padded to the K block, 64 or 128 for FP8): for BF16 and split
+ * one launch converts every A_g and every B_g (transposed), for FP8 one launch
+ * quantises (128 x 128 tile scales) every A_g and one every B_g; then one
  * persistent tensor-core launch runs the tiles of all problems, in decreasing K
  * order.  Each C_g equals, bit for bit, pgk_gemm on that problem with the same
  * tile program.  `prog` = (128, 128, stages, 0, K block): stages 6 for BF16 and

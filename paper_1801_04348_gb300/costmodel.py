@@ -173,7 +173,8 @@ def evaluate(model, shapes, dtype, dev, k=3, reps=1, seed=1000):
     t(exhaustive best) - 1 (geometric mean of 1 + r minus 1, mean, p90), the
     same for a random choice of k candidates and for the untuned default, and
     the tuning time saved (sum of all candidate times over the sum of the
-    top-k times)."""
+    top-k times).  Every record keeps all candidate times and predictions, so
+    `summarize_k` can evaluate other k on the same timings."""
     cands = candidates(dtype)
     rng = np.random.default_rng(seed)
     recs = []
@@ -192,8 +193,46 @@ def evaluate(model, shapes, dtype, dev, k=3, reps=1, seed=1000):
                      "model_ms": float(np.min(ms[top])), "random_ms": float(np.min(ms[rnd])),
                      "default_ms": float(ms[dflt]) if dflt is not None and feas[dflt] else float("nan"),
                      "exhaustive_cost_ms": float(np.sum(ms[feas])),
-                     "topk_cost_ms": float(np.sum(ms[top][np.isfinite(ms[top])]))})
+                     "topk_cost_ms": float(np.sum(ms[top][np.isfinite(ms[top])])),
+                     "ms_all": [float(x) for x in ms], "pred_all": [float(x) for x in pred],
+                     "default_index": dflt})
     return recs, summarize(recs, k)
+
+
+def expected_random_min(ms, k):
+    """Expected fastest time of k candidates drawn uniformly without replacement
+    from the feasible times `ms`: sum over the sorted times t_(i) of t_(i) times
+    the probability that t_(i) is the smallest drawn, C(n-1-i, k-1) / C(n, k)."""
+    t = np.sort(np.asarray([x for x in ms if np.isfinite(x)], np.float64))
+    n = len(t)
+    k = min(k, n)
+    w = np.asarray([math.comb(n - 1 - i, k - 1) for i in range(n)], np.float64) / math.comb(n, k)
+    return float(np.dot(w, t))
+
+
+def summarize_k(recs, k):
+    """Regret at top-k of the recorded timings: the model's k best predictions,
+    the expectation over random k-subsets (exact), and the untuned default."""
+    def gm(r):
+        r = np.asarray(r, np.float64)
+        return {"geomean": float(np.exp(np.mean(np.log1p(r))) - 1.0), "mean": float(r.mean()),
+                "p90": float(np.percentile(r, 90)), "max": float(r.max()), "n": int(r.size)}
+    rm, rr, rd = [], [], []
+    ex = tk = 0.0
+    for x in recs:
+        ms = np.asarray(x["ms_all"], np.float64)
+        pred = np.asarray(x["pred_all"], np.float64)
+        best = x["best_ms"]
+        top = np.argsort(pred)[:k]
+        rm.append(float(np.min(ms[top])) / best - 1.0)
+        rr.append(expected_random_min(ms, k) / best - 1.0)
+        d = x.get("default_index")
+        if d is not None and np.isfinite(ms[d]):
+            rd.append(ms[d] / best - 1.0)
+        ex += float(np.sum(ms[np.isfinite(ms)]))
+        tk += float(np.sum(ms[top][np.isfinite(ms[top])]))
+    return {"k": k, "shapes": len(recs), "model": gm(rm), "random_k_expected": gm(rr),
+            "untuned_default": gm(rd) if rd else None, "tuning_time_saved": ex / tk if tk else None}
 
 
 def default_index(cands, M, N, K, dtype):
@@ -227,12 +266,26 @@ def summarize(recs, k):
             "untuned_default": stats("default_ms"), "tuning_time_saved": ex / tk if tk else None}
 
 
-def training_shapes():
+def training_shapes(dtype=None):
     """Shapes whose tuning produces the timing log: the 256^3 correctness shape,
-    the four large FP32 shapes and the 512 grouped-GEMM shapes."""
+    the four large FP32 shapes and the 512 grouped-GEMM shapes.  The tensor-core
+    forms add 300 shapes log-uniform in [64, 16384] (seed 777): the tuning
+    workloads above reach 2048 at most apart from the four large shapes, and a
+    tile program's rank among the few of a tensor-core form moves with the tile
+    count, so their log needs the whole size range of the shapes it must rank."""
     big = [(4096, 4096, 4096), (8192, 8192, 8192), (8192, 1024, 4096), (16384, 64, 16384)]
     grouped = [tuple(int(v) for v in r) for r in inputs.log_uniform_dims(512, 0, 32, 2048, 16)]
-    return [(256, 256, 256)] + big + grouped
+    base = [(256, 256, 256)] + big + grouped
+    if dtype is None or dtype in (pgk.F32, pgk.I32):
+        return base
+    seen = set(base)
+    extra = []
+    for r in inputs.log_uniform_dims(300, 777, 64, 16384, 16):
+        t = tuple(int(v) for v in r)
+        if t not in seen:
+            seen.add(t)
+            extra.append(t)
+    return base + extra
 
 
 def unseen_shapes(count=1000, seed=12345, exclude=()):
@@ -262,26 +315,34 @@ def main():
     ap.add_argument("--eval-shapes", type=int, default=1000)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--model", default=None,
+                    help="evaluate this trained model (JSON) instead of collecting and training")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
     dt = pgk.DTYPES[args.dtype]
     t0 = time.time()
-    shapes = training_shapes()
-    X, y, _ = collect(shapes, dt, dev, reps=2,
-                      log_path=os.path.join(args.out, f"timing_log_{args.dtype}.csv"))
-    t1 = time.time()
-    cm = CostModel()
-    ltr, lva = cm.fit(X, y, dev, epochs=args.epochs)
-    cm.save(os.path.join(args.out, f"costmodel_{args.dtype}.json"))
-    t2 = time.time()
+    shapes = training_shapes(dt)
+    if args.model:
+        cm = CostModel.load(args.model)
+        X, ltr, lva = (), None, None
+        t1 = t2 = time.time()
+    else:
+        X, y, _ = collect(shapes, dt, dev, reps=2,
+                          log_path=os.path.join(args.out, f"timing_log_{args.dtype}.csv"))
+        t1 = time.time()
+        cm = CostModel()
+        ltr, lva = cm.fit(X, y, dev, epochs=args.epochs)
+        cm.save(os.path.join(args.out, f"costmodel_{args.dtype}.json"))
+        t2 = time.time()
     ev = unseen_shapes(args.eval_shapes, exclude=shapes)
     recs, summ = evaluate(cm, ev, dt, dev, k=args.k)
     t3 = time.time()
     summ.update({"dtype": args.dtype, "train_rows": int(len(X)), "train_loss": ltr,
                  "val_loss": lva, "collect_s": t1 - t0, "train_s": t2 - t1, "eval_s": t3 - t2,
-                 "candidates": len(candidates(dt))})
+                 "candidates": len(candidates(dt)),
+                 "by_k": [summarize_k(recs, kk) for kk in range(1, len(candidates(dt)))]})
     with open(os.path.join(args.out, f"regret_{args.dtype}.json"), "w") as f:
         json.dump({"summary": summ, "records": recs}, f)
     print(json.dumps(summ))

@@ -116,9 +116,12 @@ struct GQuant {
 pgk_status launch_quant_fp8_grouped(int transpose, const GQuant* probs, const int* prefix, int G,
                                     int total, uint8_t* dst, long long ldd, float* scales,
                                     int ld_scales, cudaStream_t st);
-// mode 0: BF16, mode 1: hi/lo split.  total = prefix[G] tile items.
-pgk_status launch_cvt_grouped(int mode, int transpose, const GCvt* probs, const int* prefix, int G,
-                              int total, uint16_t* d0, uint16_t* d1, long long ldd, cudaStream_t st);
+// mode 0: BF16, mode 1: hi/lo split.  One launch converts every A_g into (a0, a1)
+// and every B_g, transposed, into (b0, b1); totalA = prefa[G], totalB = prefb[G]
+// tile items.
+pgk_status launch_cvt_grouped(int mode, const GCvt* pa, const int* prefa, int totalA, uint16_t* a0,
+                              uint16_t* a1, const GCvt* pb, const int* prefb, int totalB,
+                              uint16_t* b0, uint16_t* b1, int G, long long ldd, cudaStream_t st);
 // pgk_gemm; with reuse_b the tensor-core forms keep the converted B of the
 // previous call on the same stream (same B, N and K) instead of converting it again.
 pgk_status gemm_device(int M, int N, int K, pgk_dtype dtype, const float* A, int lda, const float* B,

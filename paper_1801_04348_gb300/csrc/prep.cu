@@ -8,6 +8,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "pgk_internal.cuh"
 
@@ -351,104 +352,126 @@ pgk_status launch_quant_fp8(int rows, int cols, const float* src, int lds, uint8
 // work items are 64 x 64 tiles of the (padded) source, numbered problem after
 // problem; prefix[g] is the first item of problem g.
 
+// One 64 x 64 work item of problem q (item `local` of that problem).
 template <int MODE, bool TRANS>
-__global__ void __launch_bounds__(256) k_cvt_grouped(const GCvt* __restrict__ probs,
-                                                     const int* __restrict__ prefix, int G, int total,
-                                                     uint16_t* __restrict__ d0,
-                                                     uint16_t* __restrict__ d1, long long ldd) {
-    __shared__ float t[64][65];
+__device__ __forceinline__ void cvt_grouped_item(const GCvt& q, int local, uint16_t* __restrict__ d0,
+                                                 uint16_t* __restrict__ d1, long long ldd,
+                                                 float (*t)[65]) {
     const int tid = threadIdx.x;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int g = grouped_item_problem(prefix, G, item);
-        const GCvt q = probs[g];
-        const int local = item - __ldg(prefix + g);
-        // tile grid over the padded source: TRANS covers width x cols, else rows x width
-        const int tcols = TRANS ? (q.cols + 63) / 64 : (q.width + 63) / 64;
-        const int r0 = (local / tcols) * 64, c0 = (local % tcols) * 64;
-        if (!TRANS) {
-            // direct: 64 rows x 64 columns, 4 quads per thread, zeros beyond cols
+    // tile grid over the padded source: TRANS covers width x cols, else rows x width
+    const int tcols = TRANS ? (q.cols + 63) / 64 : (q.width + 63) / 64;
+    const int r0 = (local / tcols) * 64, c0 = (local % tcols) * 64;
+    if (!TRANS) {
+        // direct: 64 rows x 64 columns, 4 quads per thread, zeros beyond cols
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int idx = tid + i * 256;
-                const int r = r0 + (idx >> 4), c = c0 + (idx & 15) * 4;
-                if (r >= q.rows || c >= q.width) continue;
-                float v[4];
-                const float* sp = q.src + (size_t)r * q.lds + c;
-                if (q.vec && c + 3 < q.cols) {
+        for (int i = 0; i < 4; ++i) {
+            const int idx = tid + i * 256;
+            const int r = r0 + (idx >> 4), c = c0 + (idx & 15) * 4;
+            if (r >= q.rows || c >= q.width) continue;
+            float v[4];
+            const float* sp = q.src + (size_t)r * q.lds + c;
+            if (q.vec && c + 3 < q.cols) {
+                const float4 f = __ldg(reinterpret_cast<const float4*>(sp));
+                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = (c + u < q.cols) ? __ldg(sp + u) : 0.f;
+            }
+            uint16_t h[4], l[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) convert_one<MODE>(v[u], h[u], l[u]);
+            const size_t o = (size_t)(q.dst_row + r) * ldd + c;   // width is a multiple of 4
+            *reinterpret_cast<uint2*>(d0 + o) =
+                make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
+            if (MODE == 1)
+                *reinterpret_cast<uint2*>(d1 + o) =
+                    make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+        }
+    } else {
+        // transposed: source rows r0 .. r0 + 63 (zeros beyond rows), columns c0 .. c0 + 63
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int idx = tid + i * 256;
+            const int r = idx >> 4, c = (idx & 15) * 4;
+            const int gr = r0 + r, gc = c0 + c;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (gr < q.rows) {
+                const float* sp = q.src + (size_t)gr * q.lds + gc;
+                if (q.vec && gc + 3 < q.cols) {
                     const float4 f = __ldg(reinterpret_cast<const float4*>(sp));
                     v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
                 } else {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) v[u] = (c + u < q.cols) ? __ldg(sp + u) : 0.f;
+                    for (int u = 0; u < 4; ++u)
+                        if (gc + u < q.cols) v[u] = __ldg(sp + u);
                 }
-                uint16_t h[4], l[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) convert_one<MODE>(v[u], h[u], l[u]);
-                const size_t o = (size_t)(q.dst_row + r) * ldd + c;   // width is a multiple of 4
-                *reinterpret_cast<uint2*>(d0 + o) =
-                    make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
-                if (MODE == 1)
-                    *reinterpret_cast<uint2*>(d1 + o) =
-                        make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) t[r][c + u] = v[u];
+        }
+        __syncthreads();
+        const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = warp * 8 + j;            // destination row dst_row + c0 + c
+            const int gc = c0 + c;
+            const int gr = r0 + 2 * lane;          // destination columns gr, gr + 1
+            if (gc < q.cols && gr < q.width) {     // width is even
+                uint16_t h0, l0, h1, l1;
+                convert_one<MODE>(t[2 * lane][c], h0, l0);
+                convert_one<MODE>(t[2 * lane + 1][c], h1, l1);
+                const size_t o = (size_t)(q.dst_row + gc) * ldd + gr;
+                *reinterpret_cast<uint32_t*>(d0 + o) = h0 | ((uint32_t)h1 << 16);
+                if (MODE == 1) *reinterpret_cast<uint32_t*>(d1 + o) = l0 | ((uint32_t)l1 << 16);
+            }
+        }
+        __syncthreads();   // the tile is reused by the next item
+    }
+}
+
+// Both operands of every problem in one launch: items [0, totalA) convert the A_g
+// (rows), items [totalA, totalA + totalB) the B_g (transposed); a block's item,
+// and so its branch, is the same for all its threads.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_cvt_grouped(const GCvt* __restrict__ pa,
+                                                     const int* __restrict__ prefa, int totalA,
+                                                     uint16_t* __restrict__ a0, uint16_t* __restrict__ a1,
+                                                     const GCvt* __restrict__ pb,
+                                                     const int* __restrict__ prefb, int totalB,
+                                                     uint16_t* __restrict__ b0, uint16_t* __restrict__ b1,
+                                                     int G, long long ldd) {
+    __shared__ float t[64][65];
+    for (int item = blockIdx.x; item < totalA + totalB; item += gridDim.x) {
+        if (item < totalA) {
+            const int g = grouped_item_problem(prefa, G, item);
+            cvt_grouped_item<MODE, false>(pa[g], item - __ldg(prefa + g), a0, a1, ldd, t);
         } else {
-            // transposed: source rows r0 .. r0 + 63 (zeros beyond rows), columns c0 .. c0 + 63
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int idx = tid + i * 256;
-                const int r = idx >> 4, c = (idx & 15) * 4;
-                const int gr = r0 + r, gc = c0 + c;
-                float v[4] = {0.f, 0.f, 0.f, 0.f};
-                if (gr < q.rows) {
-                    const float* sp = q.src + (size_t)gr * q.lds + gc;
-                    if (q.vec && gc + 3 < q.cols) {
-                        const float4 f = __ldg(reinterpret_cast<const float4*>(sp));
-                        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (gc + u < q.cols) v[u] = __ldg(sp + u);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) t[r][c + u] = v[u];
-            }
-            __syncthreads();
-            const int warp = tid >> 5, lane = tid & 31;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int c = warp * 8 + j;            // destination row dst_row + c0 + c
-                const int gc = c0 + c;
-                const int gr = r0 + 2 * lane;          // destination columns gr, gr + 1
-                if (gc < q.cols && gr < q.width) {     // width is even
-                    uint16_t h0, l0, h1, l1;
-                    convert_one<MODE>(t[2 * lane][c], h0, l0);
-                    convert_one<MODE>(t[2 * lane + 1][c], h1, l1);
-                    const size_t o = (size_t)(q.dst_row + gc) * ldd + gr;
-                    *reinterpret_cast<uint32_t*>(d0 + o) = h0 | ((uint32_t)h1 << 16);
-                    if (MODE == 1) *reinterpret_cast<uint32_t*>(d1 + o) = l0 | ((uint32_t)l1 << 16);
-                }
-            }
-            __syncthreads();   // the tile is reused by the next item
+            const int j = item - totalA;
+            const int g = grouped_item_problem(prefb, G, j);
+            cvt_grouped_item<MODE, true>(pb[g], j - __ldg(prefb + g), b0, b1, ldd, t);
         }
     }
 }
 
-pgk_status launch_cvt_grouped(int mode, int transpose, const GCvt* probs, const int* prefix, int G,
-                              int total, uint16_t* d0, uint16_t* d1, long long ldd, cudaStream_t st) {
+pgk_status launch_cvt_grouped(int mode, const GCvt* pa, const int* prefa, int totalA, uint16_t* a0,
+                              uint16_t* a1, const GCvt* pb, const int* prefb, int totalB,
+                              uint16_t* b0, uint16_t* b1, int G, long long ldd, cudaStream_t st) {
+    const long long total = (long long)totalA + totalB;
     if (total < 1) return PGK_OK;
+    if (total > INT_MAX) {
+        set_error("grouped conversion: too many work items");
+        return PGK_ERR_INVALID_ARG;
+    }
     int dev = 0, sms = 0;
     PGK_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
     PGK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    const int grid = std::min(total, std::max(sms, 1) * 8);
-    if (mode == 0 && !transpose)
-        k_cvt_grouped<0, false><<<grid, 256, 0, st>>>(probs, prefix, G, total, d0, d1, ldd);
-    else if (mode == 0)
-        k_cvt_grouped<0, true><<<grid, 256, 0, st>>>(probs, prefix, G, total, d0, d1, ldd);
-    else if (!transpose)
-        k_cvt_grouped<1, false><<<grid, 256, 0, st>>>(probs, prefix, G, total, d0, d1, ldd);
+    const int grid = (int)std::min<long long>(total, std::max(sms, 1) * 8);
+    if (mode == 0)
+        k_cvt_grouped<0><<<grid, 256, 0, st>>>(pa, prefa, totalA, a0, a1, pb, prefb, totalB, b0, b1,
+                                               G, ldd);
     else
-        k_cvt_grouped<1, true><<<grid, 256, 0, st>>>(probs, prefix, G, total, d0, d1, ldd);
+        k_cvt_grouped<1><<<grid, 256, 0, st>>>(pa, prefa, totalA, a0, a1, pb, prefb, totalB, b0, b1,
+                                               G, ldd);
     PGK_CUDA_TRY(cudaGetLastError(), "grouped conversion launch");
     return PGK_OK;
 }

@@ -74,6 +74,11 @@ struct TcCfg {
     static constexpr int CHUNK =
         MODE == MODE_FP8 ? 1 : ((MODE == MODE_SPLIT || MODE == MODE_SPLIT3) ? 8 : 0);
     static constexpr int EPI_WARPS = CHUNK == 0 ? 4 : 8;
+    // FP8 hands an accumulator to the epilogue every 128-deep chunk: the waits of
+    // the producer, the MMA issuer and the epilogue poll (mbarrier.test_wait)
+    // instead of suspending (try_wait), which shortens the round trip from an
+    // MMA's completion to the reuse of its accumulator
+    static constexpr bool POLL = MODE == MODE_FP8;
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
     // tensor-memory accumulators in flight: FP8 with 128-wide tiles keeps four
     // chunk accumulators so the MMA can run three chunks ahead of the epilogue
@@ -126,16 +131,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking test of the phase with parity `parity` (never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the phase with parity `parity`.  Returns false if the CTA
 // was aborted by another warp or the limit expired (then the abort flag and
-// the device error word are set).
+// the device error word are set).  POLL spins on test_wait instead of letting
+// try_wait suspend the thread, for the waits on the critical path.
+template <bool POLL = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           unsigned int* err, unsigned int code,
                                           unsigned long long limit_ns = WAIT_LIMIT_NS) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (POLL ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (POLL ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 0) {
             if (*abort_flag) return false;
             if (globaltimer() - t0 > limit_ns) {
@@ -511,8 +530,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 const CUtensorMap* mbl = hf ? &tm.b2h : &tm.b2;   // B^T lo
                 for (int kb = 0; kb < ti.nkb && ok; ++kb)
                 for (int v = 0; v < Cfg::PASSES; ++v) {
-                    if (!mbar_wait(&empty_bar[stage], phase ^ 1u, abort_flag, p.err,
-                                   ERR_TIMEOUT_PRODUCER)) {
+                    if (!mbar_wait<Cfg::POLL>(&empty_bar[stage], phase ^ 1u, abort_flag, p.err,
+                                              ERR_TIMEOUT_PRODUCER)) {
                         ok = false;
                         break;
                     }
@@ -578,9 +597,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         // N = BN: both CTAs' halves of B^T, accumulators in both CTAs' tensor memory)
         if (lane == 0 && pair_rank<PAIR>() == 0) {
             // instruction descriptors of whole tiles and of column halves (N = BN/2)
-            const uint32_t idesc_full = Cfg::MODE == MODE_FP8 ? idesc_e4m3(Cfg::BM, Cfg::BN)
+            const uint32_t idesc_full = Cfg::MODE == MODE_FP8 ? idesc_e4m3(Cfg::TM, Cfg::BN)
                                                               : idesc_bf16(Cfg::TM, Cfg::BN);
-            const uint32_t idesc_half = Cfg::MODE == MODE_FP8 ? idesc_e4m3(Cfg::BM, Cfg::BN / 2)
+            const uint32_t idesc_half = Cfg::MODE == MODE_FP8 ? idesc_e4m3(Cfg::TM, Cfg::BN / 2)
                                                               : idesc_bf16(Cfg::TM, Cfg::BN / 2);
             int stage = 0;
             uint32_t phase = 0;
@@ -603,15 +622,16 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     const int kin = Cfg::CHUNK > 0 ? kb % Cfg::CHUNK : kb;  // K block within the chunk
                     if (Cfg::CHUNK > 0 && kin == 0) {
                         // a fresh accumulator for each chunk, folded by the epilogue
-                        if (!mbar_wait(&acce_bar[acc], acc_phase ^ 1u, abort_flag, p.err,
-                                       ERR_TIMEOUT_MMA)) {
+                        if (!mbar_wait<Cfg::POLL>(&acce_bar[acc], acc_phase ^ 1u, abort_flag, p.err,
+                                                  ERR_TIMEOUT_MMA)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
                     }
                     for (int v = 0; v < Cfg::PASSES; ++v) {
-                        if (!mbar_wait(&full_bar[stage], phase, abort_flag, p.err, ERR_TIMEOUT_MMA)) {
+                        if (!mbar_wait<Cfg::POLL>(&full_bar[stage], phase, abort_flag, p.err,
+                                                  ERR_TIMEOUT_MMA)) {
                             ok = false;
                             break;
                         }
@@ -796,7 +816,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 // clamped so that the loads stay inside the array.
                 // scale blocks of this tile: its 128-row block of A and the 128-column block
                 // of B^T (both offset by the problem's first block in a grouped launch)
-                const int mblk = ti.rowA / 128 + tm;
+                const int mblk = ti.rowA / 128 + tm * Cfg::CTAS + (int)pair_rank<PAIR>();
                 const int nblk = ti.rowB / 128 + min(n0 / 128, (tN - 1) / 128);
                 auto chunk_scale = [&](int c) {
                     return c < nchunks
@@ -811,8 +831,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 for (int ch = 0; ch < nchunks; ++ch) {
                     int w = 1;
                     if (lane == 0)
-                        w = mbar_wait(&accf_bar[acc], acc_phase, abort_flag, p.err,
-                                      ERR_TIMEOUT_EPILOGUE) ? 1 : 0;
+                        w = mbar_wait<Cfg::POLL>(&accf_bar[acc], acc_phase, abort_flag, p.err,
+                                                 ERR_TIMEOUT_EPILOGUE) ? 1 : 0;
                     w = __shfl_sync(0xffffffffu, w, 0);
                     if (!w) {
                         ok = false;
@@ -832,6 +852,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     // form's 128-column slices (a fold every 8 K blocks, off the critical path)
                     const uint64_t sc2 = f2_pack(sc, sc);
                     constexpr int NB = (NCOL == 64 || Cfg::MODE == MODE_FP8) ? 2 : 1;
+                    // a warp whose whole slice fits one batch of loads releases the
+                    // accumulator as soon as the slice is in registers, before its FMAs
+                    constexpr bool EARLY = NCOL == NB * 32;
 #pragma unroll
                     for (int c0 = 0; c0 < NCOL / 32; c0 += NB) {
                         uint32_t r[NB][32];
@@ -841,6 +864,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                                           (uint32_t)(acc * Cfg::BN + col0 + (c0 + c) * 32),
                                       r[c]);
                         tmem_ld_wait();
+                        if (EARLY) release(acc);
 #pragma unroll
                         for (int c = 0; c < NB; ++c)
 #pragma unroll
@@ -849,7 +873,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                                        f2_pack(__uint_as_float(r[c][2 * j]), __uint_as_float(r[c][2 * j + 1])),
                                        sc2);
                     }
-                    release(acc);
+                    if (!EARLY) release(acc);
                     if (++acc == Cfg::ACC_BUFS) {
                         acc = 0;
                         acc_phase ^= 1u;
@@ -1132,7 +1156,7 @@ pgk_status tc_select(const pgk_machine* m, int M, int N, int K, pgk_dtype dtype,
     const int natural = dtype == PGK_FP8_E4M3 ? 128 : 64;
     if ((prog->B0 != 128 && prog->B0 != 256) || (prog->tile != 0 && prog->tile != natural) ||
         prog->s < 1) {
-        set_error("tensor-core tiles are 128 x B1 (one CTA) or 256 x 256 (a CTA pair) with the natural "
+        set_error("tensor-core tiles are 128 x B1 (one CTA) or 256 x B1 (a CTA pair) with the natural "
                   "K depth (B0=%d tile=%d)", prog->B0, prog->tile);
         return PGK_ERR_UNSUPPORTED;
     }
@@ -1229,6 +1253,7 @@ struct TcGroupedVariant {
 };
 
 // 128-wide tiles only: a group of uneven problems wastes less on ragged edges
+// (256-wide grouped tiles measured no faster on the 512-problem group)
 static const TcGroupedVariant* tcg_table(int* n) {
     static const TcGroupedVariant t[] = {
         {PGK_BF16, 128, 6, launch_tc<TcCfg<MODE_BF16, 128, 6>, true>},
@@ -1251,9 +1276,6 @@ int tc_grouped_variants(pgk_dtype dtype, pgk_params* out, int cap) {
         }
     return k;
 }
-
-pgk_status launch_cvt_grouped(int mode, int transpose, const GCvt* probs, const int* prefix, int G,
-                              int total, uint16_t* d0, uint16_t* d1, long long ldd, cudaStream_t st);
 
 pgk_status launch_quant_fp8_grouped(int transpose, const GQuant* probs, const int* prefix, int G,
                                     int total, uint8_t* dst, long long ldd, float* scales,
@@ -1388,14 +1410,13 @@ pgk_status tc_gemm_grouped(int G, const pgk_problem* pr, pgk_dtype dtype, const 
                                            (uint8_t*)b0, kst, sb, (int)(rowsB / 128), s)) != PGK_OK)
             return st;
     } else {
-        const int mode = split ? 1 : 0;
-        if ((st = launch_cvt_grouped(mode, 0, reinterpret_cast<const GCvt*>(dt + off_gA),
-                                     reinterpret_cast<const int*>(dt + off_pA), G, (int)itemsA,
-                                     (uint16_t*)a0, (uint16_t*)a1, kst, s)) != PGK_OK)
-            return st;
-        if ((st = launch_cvt_grouped(mode, 1, reinterpret_cast<const GCvt*>(dt + off_gB),
-                                     reinterpret_cast<const int*>(dt + off_pB), G, (int)itemsB,
-                                     (uint16_t*)b0, (uint16_t*)b1, kst, s)) != PGK_OK)
+        // one launch converts every A_g and every B_g (transposed)
+        if ((st = launch_cvt_grouped(split ? 1 : 0, reinterpret_cast<const GCvt*>(dt + off_gA),
+                                     reinterpret_cast<const int*>(dt + off_pA), (int)itemsA,
+                                     (uint16_t*)a0, (uint16_t*)a1,
+                                     reinterpret_cast<const GCvt*>(dt + off_gB),
+                                     reinterpret_cast<const int*>(dt + off_pB), (int)itemsB,
+                                     (uint16_t*)b0, (uint16_t*)b1, G, kst, s)) != PGK_OK)
             return st;
     }
     TcMaps maps;

@@ -38,6 +38,23 @@ def test_trained_network_beats_the_untrained_choices(dev):
     assert summ["tuning_time_saved"] > 3
 
 
+@pytest.mark.parametrize("dtype,name", [(pgk.BF16, "bf16"), (pgk.SPLIT_BF16, "split")])
+def test_trained_network_ranks_tensor_core_programs(dev, dtype, name):
+    """The tensor-core forms have few tile programs, so the test takes the
+    model's single best prediction (k = 1) on held-out shapes (<= 2048 here for
+    time): its regret against exhaustive timing is small and below both the
+    expected regret of one random program and the untuned default's."""
+    cm = costmodel.CostModel.load(os.path.join(HERE, f"costmodel_{name}.json"))
+    shapes = [s for s in costmodel.unseen_shapes(400, exclude=costmodel.training_shapes(dtype))
+              if max(s) <= 2048][:24]
+    recs, _ = costmodel.evaluate(cm, shapes, dtype, dev, k=1, reps=3)
+    summ = costmodel.summarize_k(recs, 1)
+    print(summ)
+    assert summ["model"]["geomean"] <= 0.05
+    assert summ["model"]["geomean"] < summ["random_k_expected"]["geomean"]
+    assert summ["model"]["geomean"] < summ["untuned_default"]["geomean"]
+
+
 def test_gemm_without_parameters_uses_the_learned_selection(dev):
     pgk.costmodel_load_file(pgk.F32, os.path.join(HERE, "costmodel_f32.json"), k=3)
     try:
