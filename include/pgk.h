@@ -103,7 +103,13 @@ typedef struct {
  *    two CTAs on the two SMs of a TPC per tile, each staging its 128 rows of A
  *    and half of the B^T rows, one tcgen05.mma with cta_group::2 and M = 256 for
  *    both); s = number of pipeline stages, sr unused (0), tile = K depth per
- *    stage (0 = natural: 64 for BF16/split, 128 for FP8). */
+ *    stage (0 = natural: 64 for BF16/split, 128 for FP8).
+ *    (128, 64, s): the fused-conversion program of the BF16 (s = 4) and split
+ *    (s = 3) forms for skinny products, N <= 64 (INFEASIBLE beyond): the GEMM
+ *    reads A in FP32 by TMA and converts it to BF16 (hi and lo) in shared
+ *    memory, so A crosses memory once; A must be 16-byte aligned with lda a
+ *    multiple of 4 (else ALIGNMENT).  pgk_gemm without parameters takes it for
+ *    N <= 64 when A qualifies. */
 typedef struct { int B0, B1, s, sr, tile; } pgk_params;
 
 /* Leaves of the case discussion, with the paper's labels (Section 5):
@@ -359,7 +365,9 @@ PGK_API pgk_status pgk_quant_fp8(int rows, int cols, const float* src, int lds, 
  * K-major.  BF16: A, Bt bf16.  SPLIT: A/A_lo and Bt/Bt_lo are the hi/lo bf16
  * pairs.  FP8: A, Bt E4M3 codes, scaleA is ceil(M/128) x ceil(K/128) and scaleB
  * ceil(K/128) x ceil(N/128) (row-major, dense).  Row strides must be multiples
- * of 16 bytes and pointers 16-byte aligned (else ALIGNMENT).  The kernel's
+ * of 16 bytes and pointers 16-byte aligned (else ALIGNMENT).  The
+ * fused-conversion programs (B1 = 64) read FP32 A and are not available here
+ * (UNSUPPORTED).  The kernel's
  * bounded waits set the device error word on timeout; the call then returns
  * OK and pgk_check_device_error() reports TIMEOUT.
  * Errors: INVALID_ARG, ALIGNMENT, UNSUPPORTED, INFEASIBLE, CUDA. */

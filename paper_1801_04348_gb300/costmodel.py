@@ -48,7 +48,9 @@ def candidates(dtype) -> list:
             if info.family == pgk.FAM_RB and info.sr == info.s and info.tile == 8:
                 out.append(pgk.params(info.B0, info.B1, info.s, info.sr, info.tile))
         return out
-    return pgk.default_candidates(dtype)
+    # the tile programs; the fused-conversion program (B1 = 64) is the case
+    # discussion's choice for N <= 64 and is not ranked
+    return [p for p in pgk.default_candidates(dtype) if p.B1 != 64]
 
 
 def feature_row(M, N, K, p, dtype) -> list:

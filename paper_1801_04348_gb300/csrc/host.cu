@@ -429,9 +429,19 @@ pgk_status gemm_device(int M, int N, int K, pgk_dtype dtype, const float* A, int
     pgk_params p;
     if (prog) {
         p = *prog;
-    } else if (pgk_tune_cache_get(M, N, K, dtype, &p) != PGK_OK &&
-               learned_select(M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, stream, &p) != PGK_OK) {
-        p = default_params(M, N, K, dtype);
+    } else if (pgk_tune_cache_get(M, N, K, dtype, &p) != PGK_OK) {
+        // skinny products in the BF16 and split forms: the fused-conversion program
+        // (A read once, in FP32, by the GEMM) is the leaf of the case discussion
+        // whenever N fits its 64-wide tile and A suits TMA; otherwise the learned
+        // selection ranks the tile programs, else the default
+        const bool fused = (dtype == PGK_BF16 || dtype == PGK_SPLIT_BF16) && N <= 64 &&
+                           ((uintptr_t)A & 15u) == 0 && lda % 4 == 0;
+        if (fused) {
+            p = pgk_params{128, 64, dtype == PGK_SPLIT_BF16 ? 3 : 4, 0, 0};
+        } else if (learned_select(M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, stream, &p) !=
+                   PGK_OK) {
+            p = default_params(M, N, K, dtype);
+        }
     }
     pgk_case c;
     st = select_any(&m, NULL, M, N, K, dtype, &p, &c);

@@ -187,23 +187,27 @@ static int simt_candidates(int rb_family, pgk_params* out, int cap) {
 static int tc_candidates(pgk_dtype dtype, pgk_params* out, int cap) {
     std::vector<pgk_params> c;
     // B0 = 256: a CTA pair per 256 x 256 tile (each SM stages half of B)
+    // B1 = 64 (last): the fused-conversion program, feasible for N <= 64 only
     if (dtype == PGK_SPLIT_BF16) {
         pgk_params a = {128, 128, 3, 0, 0}, b = {128, 256, 2, 0, 0}, d = {128, 256, 4, 0, 0},
-                   e = {128, 128, 6, 0, 0}, f = {256, 256, 3, 0, 0}, g = {256, 256, 6, 0, 0};
+                   e = {128, 128, 6, 0, 0}, f = {256, 256, 3, 0, 0}, g = {256, 256, 6, 0, 0},
+                   h = {128, 64, 3, 0, 0};
         c.push_back(a);
         c.push_back(b);
         c.push_back(d);
         c.push_back(e);
         c.push_back(f);
         c.push_back(g);
+        c.push_back(h);
     } else if (dtype == PGK_BF16) {
         pgk_params a = {128, 256, 4, 0, 0}, b = {128, 128, 6, 0, 0}, d = {128, 256, 3, 0, 0},
-                   e = {128, 128, 4, 0, 0}, f = {256, 256, 6, 0, 0};
+                   e = {128, 128, 4, 0, 0}, f = {256, 256, 6, 0, 0}, h = {128, 64, 4, 0, 0};
         c.push_back(a);
         c.push_back(b);
         c.push_back(d);
         c.push_back(e);
         c.push_back(f);
+        c.push_back(h);
     } else {
         pgk_params a = {128, 128, 6, 0, 0}, b = {128, 256, 4, 0, 0};
         c.push_back(a);
@@ -250,9 +254,13 @@ static std::vector<pgk_params> learned_candidates(pgk_dtype dtype) {
             }
         }
     } else {
+        // the tile programs the cost model ranks; the fused-conversion program
+        // (B1 = 64) is chosen by the case discussion for N <= 64, not ranked
         const int n = tc_candidates(dtype, NULL, 0);
-        c.resize(n);
-        tc_candidates(dtype, c.data(), n);
+        std::vector<pgk_params> all(n);
+        tc_candidates(dtype, all.data(), n);
+        for (const pgk_params& p : all)
+            if (p.B1 != 64) c.push_back(p);
     }
     return c;
 }

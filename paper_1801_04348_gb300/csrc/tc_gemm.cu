@@ -22,6 +22,7 @@
 // preparation kernels write it.  Tails in M, N and K come from TMA's zero fill.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <string.h>
@@ -51,10 +52,16 @@ static constexpr unsigned int ERR_TIMEOUT_EPILOGUE = 0x4u;
 static constexpr unsigned int ERR_TIMEOUT_DRAIN = 0x8u;
 static constexpr unsigned int ERR_TIMEOUT_SELFTEST = 0x10u;
 
-template <int MODE_, int BN_, int STAGES_, bool PAIR_ = false>
+template <int MODE_, int BN_, int STAGES_, bool PAIR_ = false, int FSTAGES_ = 0>
 struct TcCfg {
     static constexpr int MODE = MODE_, BN = BN_, STAGES = STAGES_;
     static constexpr bool PAIR = PAIR_;
+    // Fused conversion (FSTAGES > 0): A arrives in FP32 through an FSTAGES-deep ring
+    // (per K block two TMA boxes of 128 rows x 32 FP32, 128B-swizzled) and converter
+    // warps write its BF16 tiles (hi, and lo for split) into the stage ring, so A is
+    // read from memory once; only B^T (prepared, BF16) travels by TMA into the stages.
+    static constexpr int FSTAGES = FSTAGES_;
+    static constexpr bool FUSED = FSTAGES > 0;
     static constexpr int BM = 128;                          // rows of A staged (and accumulated) per CTA
     static constexpr int CTAS = PAIR ? 2 : 1;               // CTAs sharing one output tile
     static constexpr int TM = BM * CTAS;                    // rows of an output tile
@@ -73,23 +80,29 @@ struct TcCfg {
     // of the tensor-core accumulator, the dominant error at large K.
     static constexpr int CHUNK =
         MODE == MODE_FP8 ? 1 : ((MODE == MODE_SPLIT || MODE == MODE_SPLIT3) ? 8 : 0);
-    static constexpr int EPI_WARPS = CHUNK == 0 ? 4 : 8;
+    // epilogue warps: 8 fold the chunked forms' wide tiles; a fused 64-wide tile needs 4
+    static constexpr int EPI_WARPS = (CHUNK == 0 || FSTAGES_ > 0) ? 4 : 8;
     // FP8 hands an accumulator to the epilogue every 128-deep chunk: the waits of
     // the producer, the MMA issuer and the epilogue poll (mbarrier.test_wait)
     // instead of suspending (try_wait), which shortens the round trip from an
     // MMA's completion to the reuse of its accumulator
     static constexpr bool POLL = MODE == MODE_FP8;
-    static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+    static constexpr int CONV_WARPS = FUSED ? 8 : 0;        // warps after the epilogue warps
+    static constexpr int THREADS = 64 + 32 * (EPI_WARPS + CONV_WARPS);
+    static constexpr int F_BYTES = FUSED ? 2 * BM * 128 : 0;  // one FP32 K block of A (two boxes)
     // tensor-memory accumulators in flight: FP8 with 128-wide tiles keeps four
     // chunk accumulators so the MMA can run three chunks ahead of the epilogue
     static constexpr int ACC_BUFS = (MODE == MODE_FP8 && BN == 128) ? 4 : 2;
     static constexpr int TMEM_COLS = ACC_BUFS * BN;
     // epilogue staging: one 32 x 33 FP32 block per epilogue warp after the stage ring
     static constexpr int XPOSE_BYTES = EPI_WARPS * 32 * 33 * 4;
-    static constexpr int SMEM_RAW = STAGES * STAGE_BYTES + XPOSE_BYTES + 1024;
+    static constexpr int SMEM_RAW = STAGES * STAGE_BYTES + FSTAGES * F_BYTES + XPOSE_BYTES + 1024;
     // at least 116 KB so that one CTA owns the SM (and its tensor memory)
     static constexpr int SMEM = SMEM_RAW > 118784 ? SMEM_RAW : 118784;
-    static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation is a power of two");
+    static_assert(TMEM_COLS == 128 || TMEM_COLS == 256 || TMEM_COLS == 512,
+                  "TMEM allocation is a power of two");
+    static_assert(!FUSED || (!PAIR && (MODE == MODE_BF16 || MODE == MODE_SPLIT) && BN == 64),
+                  "fused conversion: single-CTA BF16 and split tiles of 128 x 64");
     static_assert(SMEM <= 232448 - 512, "stage ring, staging blocks and barriers fit the opt-in shared memory");
     static_assert(CHUNK == 0 || BN / (EPI_WARPS / 4) <= 128, "promoted columns per warp");
     static_assert(!PAIR || (MODE != MODE_FP8 && BN == 256), "CTA pairs: kind::f16 forms, 256 x 256 tiles");
@@ -386,6 +399,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
     __shared__ uint64_t accf_bar[Cfg::ACC_BUFS];
     __shared__ uint64_t acce_bar[Cfg::ACC_BUFS];
     __shared__ uint64_t drain_bar;
+    // fused conversion: the FP32 ring of A (filled by TMA, emptied by the converters)
+    __shared__ uint64_t ffull_bar[Cfg::FUSED ? Cfg::FSTAGES : 1];
+    __shared__ uint64_t fempty_bar[Cfg::FUSED ? Cfg::FSTAGES : 1];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
 
@@ -412,8 +428,13 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
-            mbar_init(&full_bar[s], 1);
+            // fused: the producer's B^T copies and one arrival per converter warp
+            mbar_init(&full_bar[s], 1 + Cfg::CONV_WARPS);
             mbar_init(&empty_bar[s], 1);
+        }
+        for (int s = 0; s < Cfg::FSTAGES; ++s) {
+            mbar_init(&ffull_bar[s], 1);
+            mbar_init(&fempty_bar[s], Cfg::CONV_WARPS);
         }
         for (int b = 0; b < Cfg::ACC_BUFS; ++b) {
             mbar_init(&accf_bar[b], 1);
@@ -509,7 +530,82 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         return ti;
     };
 
-    if (warp == 0) {
+    uint8_t* fring = tiles + (size_t)Cfg::STAGES * Cfg::STAGE_BYTES;   // FP32 ring (fused)
+    if (Cfg::FUSED && warp == 0) {
+        // ------------------------------------------------ producer (fused)
+        // per K block: the FP32 slice of A (two 128-row x 32-column boxes) into the
+        // FP32 ring, and B^T hi (and lo) into the stage the converters fill with A
+        if (lane == 0) {
+            int stage = 0, fs = 0;
+            uint32_t phase = 0, fphase = 0;
+            uint32_t issued = 0, parity = 0, fissued = 0, fparity = 0;
+            bool ok = true;
+            for (int t = tile_first<PAIR>(); t < ntiles && ok; t += tile_stride<PAIR>()) {
+                const TileInfo ti = tile_info(t);
+                const int ya = ti.tm * Cfg::TM;
+                const int yb = ti.tn * Cfg::BN;
+                for (int kb = 0; kb < ti.nkb && ok; ++kb) {
+                    const int x = kb * Cfg::BK;
+                    if (!mbar_wait<Cfg::POLL>(&fempty_bar[fs], fphase ^ 1u, abort_flag, p.err,
+                                              ERR_TIMEOUT_PRODUCER)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* fd = fring + (size_t)fs * Cfg::F_BYTES;
+                    mbar_arrive_expect_tx(&ffull_bar[fs], (uint32_t)Cfg::F_BYTES);
+                    tma_load_2d(fd, &tm.a, &ffull_bar[fs], x, ya);
+                    tma_load_2d(fd + Cfg::F_BYTES / 2, &tm.a, &ffull_bar[fs], x + 32, ya);
+                    fissued |= 1u << fs;
+                    fparity = (fparity & ~(1u << fs)) | (fphase << fs);
+                    if (++fs == Cfg::FSTAGES) {
+                        fs = 0;
+                        fphase ^= 1u;
+                    }
+                    if (!mbar_wait<Cfg::POLL>(&empty_bar[stage], phase ^ 1u, abort_flag, p.err,
+                                              ERR_TIMEOUT_PRODUCER)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = tiles + (size_t)stage * Cfg::STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full_bar[stage], (uint32_t)(Cfg::NOPS * Cfg::B_BYTES));
+                    tma_load_2d(st + Cfg::A_BYTES, &tm.b, &full_bar[stage], x, yb);
+                    if (Cfg::MODE == MODE_SPLIT)
+                        tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tm.b2, &full_bar[stage], x, yb);
+                    issued |= 1u << stage;
+                    parity = (parity & ~(1u << stage)) | (phase << stage);
+                    if (++stage == Cfg::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // drain: every issued copy must land before the CTA may exit.  A stage
+                // barrier also waits for converter arrivals that an abort may withhold,
+                // so its drain is bounded by the drain limit like every other.
+                for (int s = 0; s < Cfg::FSTAGES; ++s)
+                    if (fissued & (1u << s)) {
+                        const unsigned long long t0 = globaltimer();
+                        while (!mbar_try_wait(&ffull_bar[s], (fparity >> s) & 1u)) {
+                            if (globaltimer() - t0 > DRAIN_LIMIT_NS) {
+                                atomicOr(p.err, ERR_TIMEOUT_DRAIN);
+                                break;
+                            }
+                        }
+                    }
+                for (int s = 0; s < Cfg::STAGES; ++s)
+                    if (issued & (1u << s)) {
+                        const unsigned long long t0 = globaltimer();
+                        while (!mbar_try_wait(&full_bar[s], (parity >> s) & 1u)) {
+                            if (globaltimer() - t0 > DRAIN_LIMIT_NS) {
+                                atomicOr(p.err, ERR_TIMEOUT_DRAIN);
+                                break;
+                            }
+                        }
+                    }
+            }
+        }
+    } else if (warp == 0) {
         // ------------------------------------------------------- producer
         if (lane == 0) {
             int stage = 0;
@@ -720,6 +816,87 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             }
         }
         __syncwarp();
+    } else if (Cfg::FUSED && warp >= 2 + Cfg::EPI_WARPS) {
+        // ------------------------------------------------------- converters
+        // thread (r, h): row r of the 128-row block, FP32 box h (K columns 32h ..
+        // 32h + 31 of the 64-deep block).  The 16-byte chunk i of a 128-byte row
+        // sits at chunk i ^ (r mod 8) (128-byte swizzle) in the FP32 boxes and in
+        // the BF16 operand tiles alike, so eight consecutive rows of a quarter warp
+        // touch eight different chunks: no bank conflicts either way.
+        const int ct = (int)threadIdx.x - 32 * (2 + Cfg::EPI_WARPS);
+        const int r = ct & 127, h = ct >> 7;
+        const int rx = r & 7;
+        int stage = 0, fs = 0;
+        uint32_t phase = 0, fphase = 0;
+        bool ok = true;
+        for (int t = tile_first<PAIR>(); t < ntiles && ok; t += tile_stride<PAIR>()) {
+            const TileInfo ti = tile_info(t);
+            for (int kb = 0; kb < ti.nkb; ++kb) {
+                int w = 1;
+                if (lane == 0)
+                    w = (mbar_wait<Cfg::POLL>(&ffull_bar[fs], fphase, abort_flag, p.err,
+                                              ERR_TIMEOUT_PRODUCER) &&
+                         mbar_wait<Cfg::POLL>(&empty_bar[stage], phase ^ 1u, abort_flag, p.err,
+                                              ERR_TIMEOUT_PRODUCER)) ? 1 : 0;
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (!w) {
+                    ok = false;
+                    break;
+                }
+                // every lane observes both completed phases (lane 0 already has)
+                while (!mbar_test_wait(&ffull_bar[fs], fphase)) {
+                }
+                while (!mbar_test_wait(&empty_bar[stage], phase ^ 1u)) {
+                }
+                const uint8_t* src = fring + (size_t)fs * Cfg::F_BYTES + h * (Cfg::F_BYTES / 2) + r * 128;
+                float4 v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    v[i] = *reinterpret_cast<const float4*>(src + ((i ^ rx) << 4));
+                // the FP32 slot is free once every lane of every converter warp has read it
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&fempty_bar[fs]);
+                uint8_t* dhi = tiles + (size_t)stage * Cfg::STAGE_BYTES + r * 128;
+                uint8_t* dlo = dhi + Cfg::A_BYTES + Cfg::B_BYTES;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    // K columns 32h + 8i .. 32h + 8i + 7 -> 16-byte chunk 4h + i of the BF16 row
+                    const float x[8] = {v[2 * i].x, v[2 * i].y, v[2 * i].z, v[2 * i].w,
+                                        v[2 * i + 1].x, v[2 * i + 1].y, v[2 * i + 1].z, v[2 * i + 1].w};
+                    // a pair of columns per 32-bit word, lower column in the lower half:
+                    // hi = bf16(x) and lo = bf16(x - hi), both rounded to nearest even
+                    // (x - hi is exact in FP32)
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const __nv_bfloat162 hp = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+                        hw[j] = *reinterpret_cast<const uint32_t*>(&hp);
+                        if (Cfg::MODE == MODE_SPLIT) {
+                            const float2 hf = __bfloat1622float2(hp);
+                            const __nv_bfloat162 lp =
+                                __floats2bfloat162_rn(x[2 * j] - hf.x, x[2 * j + 1] - hf.y);
+                            lw[j] = *reinterpret_cast<const uint32_t*>(&lp);
+                        }
+                    }
+                    const int off = ((4 * h + i) ^ rx) << 4;
+                    *reinterpret_cast<uint4*>(dhi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    if (Cfg::MODE == MODE_SPLIT)
+                        *reinterpret_cast<uint4*>(dlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+                // the tensor cores read the tiles through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full_bar[stage]);
+                if (++fs == Cfg::FSTAGES) {
+                    fs = 0;
+                    fphase ^= 1u;
+                }
+                if (++stage == Cfg::STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
     } else {
         // -------------------------------------------------------- epilogue
         const int e = warp - 2;
@@ -727,7 +904,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
         // a thread holds 32 consecutive columns of its own row after tcgen05.ld; the
         // block goes through this warp's shared staging (pitch 33: conflict-free both
         // ways) so that every store instruction covers 32 consecutive columns of a row
-        float* xp = reinterpret_cast<float*>(tiles + (size_t)Cfg::STAGES * Cfg::STAGE_BYTES) +
+        float* xp = reinterpret_cast<float*>(tiles + (size_t)Cfg::STAGES * Cfg::STAGE_BYTES +
+                                             (size_t)Cfg::FSTAGES * Cfg::F_BYTES) +
                     e * (32 * 33);
         auto store_block = [&](const float (&v)[32], int row0, int cb, int M, int N, float* C,
                                int ldc) {
@@ -838,7 +1016,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                         ok = false;
                         break;
                     }
-                    while (!mbar_try_wait(&accf_bar[acc], acc_phase)) {
+                    // every lane observes the completed phase (lane 0 already has)
+                    while (!(Cfg::POLL ? mbar_test_wait(&accf_bar[acc], acc_phase)
+                                       : mbar_try_wait(&accf_bar[acc], acc_phase))) {
                     }
                     tc_fence_after();
                     const float sc = Cfg::MODE == MODE_FP8 ? __shfl_sync(0xffffffffu, sc_cur, ch & 31) : 1.f;
@@ -982,8 +1162,9 @@ static pgk_status get_encoder() {
     return PGK_OK;
 }
 
-// 2D K-major tensor map: rows x K elements, row stride ld elements, box
-// (128 bytes of K) x box_rows, 128-byte swizzle, zero fill out of bounds.
+// 2D K-major tensor map: rows x K elements of esz bytes (1: E4M3 codes, 2: BF16,
+// 4: FP32), row stride ld elements, box (128 bytes of K) x box_rows, 128-byte
+// swizzle, zero fill out of bounds.
 static pgk_status make_map(CUtensorMap* map, const void* base, int rows, int K, int ld, int esz,
                            int box_rows) {
     if (((uintptr_t)base & 15u) != 0 || ((long long)ld * esz) % 16 != 0) {
@@ -994,7 +1175,10 @@ static pgk_status make_map(CUtensorMap* map, const void* base, int rows, int K, 
     cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
     cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+    const CUtensorMapDataType ty = esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                              : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    CUresult r = g_encode(map, ty,
                           2, const_cast<void*>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1090,19 +1274,21 @@ static cudaError_t launch_tc(const TcMaps& maps, const TcParams& p0, long long t
 struct TcVariant {
     int family, BM, BN, stages, smem, threads, tmem_cols;
     int b_box;   // rows of B^T per tensor-map box (per CTA)
+    int fused;   // 1: A is read in FP32 and converted inside the GEMM
     const void* func;
     tc_launch_fn launch;
 };
 
-template <int MODE, int BN, int ST, bool PAIR = false>
+template <int MODE, int BN, int ST, bool PAIR = false, int FST = 0>
 static TcVariant tcv(int family) {
-    typedef TcCfg<MODE, BN, ST, PAIR> Cfg;
+    typedef TcCfg<MODE, BN, ST, PAIR, FST> Cfg;
     TcVariant v = {family, Cfg::TM, BN, ST, Cfg::SMEM, Cfg::THREADS, Cfg::TMEM_COLS, Cfg::BNL,
-                   (const void*)k_tc_gemm<Cfg>, launch_tc<Cfg, false>};
+                   Cfg::FUSED ? 1 : 0, (const void*)k_tc_gemm<Cfg>, launch_tc<Cfg, false>};
     return v;
 }
 
-// B0 = 128: one CTA per 128 x B1 tile; B0 = 256: a CTA pair per 256 x 256 tile
+// B0 = 128: one CTA per 128 x B1 tile; B0 = 256: a CTA pair per 256 x 256 tile;
+// B1 = 64: the fused-conversion programs of the BF16 and split forms
 static const TcVariant* tc_table(int* n) {
     static const TcVariant t[] = {
         tcv<MODE_BF16, 256, 4>(PGK_FAM_TC_BF16),   tcv<MODE_BF16, 128, 6>(PGK_FAM_TC_BF16),
@@ -1113,6 +1299,9 @@ static const TcVariant* tc_table(int* n) {
         tcv<MODE_BF16, 256, 6, true>(PGK_FAM_TC_BF16),
         tcv<MODE_SPLIT3, 256, 6, true>(PGK_FAM_TC_SPLIT),
         tcv<MODE_SPLIT, 256, 3, true>(PGK_FAM_TC_SPLIT),
+        // B1 = 64: A converted inside the GEMM (skinny products, N <= 64)
+        tcv<MODE_SPLIT, 64, 3, false, 2>(PGK_FAM_TC_SPLIT),
+        tcv<MODE_BF16, 64, 4, false, 3>(PGK_FAM_TC_BF16),
     };
     *n = (int)(sizeof(t) / sizeof(t[0]));
     return t;
@@ -1171,6 +1360,13 @@ pgk_status tc_select(const pgk_machine* m, int M, int N, int K, pgk_dtype dtype,
                       t[i].smem, m->smem_per_block_optin, m->cc_major, m->cc_minor);
             return PGK_ERR_INFEASIBLE;
         }
+        // the fused program covers all N columns with one 64-wide tile, so every A
+        // element is converted once
+        if (t[i].fused && N > t[i].BN) {
+            set_error("the fused-conversion program (B1 = %d) covers N <= %d, not N = %d", t[i].BN,
+                      t[i].BN, N);
+            return PGK_ERR_INFEASIBLE;
+        }
         pgk_case c;
         memset(&c, 0, sizeof(c));
         c.leaf = PGK_LEAF_4A3A;
@@ -1202,6 +1398,10 @@ pgk_status tc_gemm_launch(const pgk_case& c, int M, int N, int K, pgk_dtype dtyp
     if (i < 0 || i >= n || t[i].family != family_of(dtype)) {
         set_error("case does not name a tensor-core variant of this form");
         return PGK_ERR_INVALID_ARG;
+    }
+    if (t[i].fused) {
+        set_error("the fused-conversion program (B1 = 64) takes FP32 A: call pgk_gemm");
+        return PGK_ERR_UNSUPPORTED;
     }
     const int esz = dtype == PGK_FP8_E4M3 ? 1 : 2;
     TcMaps maps;
@@ -1456,11 +1656,70 @@ pgk_status launch_split_bf16(int rows, int cols, const float* src, int lds, uint
 pgk_status launch_quant_fp8(int rows, int cols, const float* src, int lds, uint8_t* dst, int ldd,
                             float* scales, int ld_scales, int transpose, cudaStream_t st);
 
+// The fused-conversion programs: B^T is prepared (BF16, or hi and lo) into a
+// library workspace, A is read in FP32 by the kernel itself.
+static pgk_status tc_gemm_fused(const TcVariant& v, int M, int N, int K, pgk_dtype dtype,
+                                const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                                int beta, cudaStream_t s, bool prep_b) {
+    pgk_status st = get_encoder();
+    if (st != PGK_OK) return st;
+    if (((uintptr_t)A & 15u) != 0 || lda % 4 != 0) {
+        set_error("the fused-conversion program reads A by TMA: A must be 16-byte aligned with lda "
+                  "a multiple of 4");
+        return PGK_ERR_ALIGNMENT;
+    }
+    const int Kp = (K + 15) / 16 * 16;
+    void* b0 = workspace(WS_B0, (size_t)N * Kp * 2, &st);
+    if (!b0) return st;
+    void* b1 = nullptr;
+    if (dtype == PGK_SPLIT_BF16 && !(b1 = workspace(WS_B1, (size_t)N * Kp * 2, &st))) return st;
+    if (prep_b) {
+        st = dtype == PGK_SPLIT_BF16
+                 ? launch_split_bf16(K, N, B, ldb, (uint16_t*)b0, (uint16_t*)b1, Kp, 1, s)
+                 : launch_cvt_bf16(K, N, B, ldb, (uint16_t*)b0, Kp, 1, s);
+        if (st != PGK_OK) return st;
+    }
+    TcMaps maps;
+    if ((st = make_map(&maps.a, A, M, K, lda, 4, 128)) != PGK_OK) return st;
+    if ((st = make_map(&maps.b, b0, N, K, Kp, 2, v.b_box)) != PGK_OK) return st;
+    if (b1) {
+        if ((st = make_map(&maps.b2, b1, N, K, Kp, 2, v.b_box)) != PGK_OK) return st;
+    } else {
+        maps.b2 = maps.b;
+    }
+    maps.a2 = maps.a;
+    maps.bh = maps.b;
+    maps.b2h = maps.b2;
+    pgk_machine m;
+    if ((st = current_machine(&m, NULL)) != PGK_OK) return st;
+    TcParams p;
+    memset(&p, 0, sizeof(p));
+    p.M = M;
+    p.N = N;
+    p.K = K;
+    p.C = C;
+    p.ldc = ldc;
+    p.beta = beta ? 1 : 0;
+    p.err = device_error_word(&st);
+    if (!p.err) return st;
+    const long long tiles = (long long)((M + v.BM - 1) / v.BM) * ((N + v.BN - 1) / v.BN);
+    cudaError_t e = v.launch(maps, p, tiles, m.sm_count, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused-conversion GEMM launch");
+    return PGK_OK;
+}
+
 // FP32 operands -> library workspaces (K padded to a multiple of 16 elements)
-// -> tensor-core kernel.
+// -> tensor-core kernel; the fused-conversion programs read A in FP32 themselves.
 pgk_status tc_gemm_fp32_inputs(const pgk_case& c, int M, int N, int K, pgk_dtype dtype,
                                const float* A, int lda, const float* B, int ldb, float* C, int ldc,
                                int beta, cudaStream_t s, bool prep_b) {
+    {
+        int n;
+        const TcVariant* t = tc_table(&n);
+        const int i = c.variant_id - tc_base_id;
+        if (i >= 0 && i < n && t[i].fused)
+            return tc_gemm_fused(t[i], M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, s, prep_b);
+    }
     const int Kp = (K + 15) / 16 * 16;
     const int esz = dtype == PGK_FP8_E4M3 ? 1 : 2;
     pgk_status st;

@@ -114,14 +114,23 @@ def test_tensor_core_case_selection(built):
         cands = pgk.default_candidates(form)
         assert cands
         for p in cands:
-            st, c = pgk.select_case(m, 8192, 8192, 8192, form, p, raise_on_error=False)
+            # B1 = 64: the fused-conversion program, whose one tile covers N <= 64
+            N = 64 if p.B1 == 64 else 8192
+            st, c = pgk.select_case(m, 8192, N, 8192, form, p, raise_on_error=False)
             assert st == 0, (form, p.as_tuple(), pgk.last_error())
             assert (c.params.B0, c.params.B1, c.params.s) == (p.B0, p.B1, p.s)
             assert c.smem_bytes <= m.smem_per_block_optin and c.threads <= m.max_threads_per_block
+            if p.B1 == 64:
+                st, _ = pgk.select_case(m, 8192, 65, 8192, form, p, raise_on_error=False)
+                assert st == 2, (form, p.as_tuple())
         for bad in [(256, 128, 3), (512, 256, 3), (128, 192, 4)]:
             st, _ = pgk.select_case(m, 8192, 8192, 8192, form, pgk.params(*bad, 0, 0),
                                     raise_on_error=False)
             assert st == 3, (form, bad)
+    # the fused-conversion program exists for BF16 and split, not for FP8
+    assert any(p.B1 == 64 for p in pgk.default_candidates(pgk.SPLIT_BF16))
+    assert any(p.B1 == 64 for p in pgk.default_candidates(pgk.BF16))
+    assert not any(p.B1 == 64 for p in pgk.default_candidates(pgk.FP8_E4M3))
     # CTA pairs exist for the kind::f16 forms only
     assert any(p.B0 == 256 for p in pgk.default_candidates(pgk.SPLIT_BF16))
     assert any(p.B0 == 256 for p in pgk.default_candidates(pgk.BF16))
