@@ -1032,9 +1032,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     // form's 128-column slices (a fold every 8 K blocks, off the critical path)
                     const uint64_t sc2 = f2_pack(sc, sc);
                     constexpr int NB = (NCOL == 64 || Cfg::MODE == MODE_FP8) ? 2 : 1;
-                    // a warp whose whole slice fits one batch of loads releases the
-                    // accumulator as soon as the slice is in registers, before its FMAs
-                    constexpr bool EARLY = NCOL == NB * 32;
+                    // the accumulator is released as soon as the warp's last batch of
+                    // columns is in registers, before that batch's FMAs
 #pragma unroll
                     for (int c0 = 0; c0 < NCOL / 32; c0 += NB) {
                         uint32_t r[NB][32];
@@ -1044,7 +1043,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                                           (uint32_t)(acc * Cfg::BN + col0 + (c0 + c) * 32),
                                       r[c]);
                         tmem_ld_wait();
-                        if (EARLY) release(acc);
+                        if (c0 + NB >= NCOL / 32) release(acc);
 #pragma unroll
                         for (int c = 0; c < NB; ++c)
 #pragma unroll
@@ -1053,7 +1052,6 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                                        f2_pack(__uint_as_float(r[c][2 * j]), __uint_as_float(r[c][2 * j + 1])),
                                        sc2);
                     }
-                    if (!EARLY) release(acc);
                     if (++acc == Cfg::ACC_BUFS) {
                         acc = 0;
                         acc_phase ^= 1u;
