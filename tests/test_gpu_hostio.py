@@ -147,3 +147,18 @@ def test_tuned_program_runs_every_panel(dev):
     ref = _device_result(dev, A, B, pgk.SPLIT_BF16, None)
     assert np.array_equal(Ch.numpy(), ref)
     assert np.array_equal(ref, _device_result(dev, A, B, pgk.SPLIT_BF16, pgk.params(256, 256, 3, 0, 0)))
+
+
+@pytest.mark.parametrize("dtype", [pgk.SPLIT_BF16, pgk.BF16])
+def test_skinny_host_buffers_take_the_fused_program(dev, dtype):
+    """N <= 64 on host buffers: without parameters every row panel runs the
+    fused-conversion program (B converted once, each panel's A read in FP32), and
+    the result equals the device path with the same program bit for bit."""
+    M, N, K = 1100, 64, 2048
+    A, B = inputs.gemm_operands(M, N, K, seed=31)
+    Ah, Bh = _host(A, True), _host(B, True)
+    Ch = _host(np.full((M, N), np.nan, np.float32), True)
+    pgk.gemm_host(Ah, Bh, Ch, dtype, None)
+    torch.cuda.synchronize()
+    fused = pgk.params(128, 64, 3 if dtype == pgk.SPLIT_BF16 else 4, 0, 0)
+    assert np.array_equal(Ch.numpy(), _device_result(dev, A, B, dtype, fused))
