@@ -152,7 +152,8 @@ def test_launch_outcome_matches_prediction(dev, machine):
 @pytest.mark.parametrize("M,N,K", [(8192, 8192, 8192), (4096, 4096, 4096), (8192, 1024, 4096),
                                    (16384, 64, 16384)])
 def test_full_size_sampled_rows(dev, M, N, K):
-    """BASELINE sizes with the default (tuned-or-default) parameters; 24 sampled
+    """The FP32 workload sizes (4096^3, 8192^3, 8192 x 1024 x 4096 and the skinny
+    16384 x 64 x 16384) with the default (tuned-or-default) parameters; 24 sampled
     rows checked against the oracle row by row."""
     A, B = inputs.gemm_operands(M, N, K, seed=0)
     rows = np.unique(np.concatenate([[0, M - 1], np.random.default_rng(0).integers(0, M, 22)]))
