@@ -74,3 +74,59 @@ def test_shape_option():
     assert bench.gemm_shape(A) == (4096, 4096, 4096)
     A.shape = "16384,64,16384"
     assert bench.gemm_shape(A) == (16384, 64, 16384)
+
+
+def test_row_errors_frobenius_and_worst_row():
+    import numpy as np
+
+    import bench
+    ref = np.array([[1.0, 0.0], [0.0, 2.0]])
+    got = np.array([[1.0, 0.1], [0.0, 2.0]])
+    frob, worst = bench.row_errors(got, ref)
+    assert frob == pytest.approx(0.1 / np.sqrt(5.0))
+    assert worst == pytest.approx(0.1)
+
+
+def test_roofline_bounds_and_peaks():
+    """FP32 against the derived SIMT peak (ALU), the tensor forms against the
+    measured BF16 peak (burst for a short timed region, sustained for a long one;
+    FP8 at twice it), the fused-conversion programs against the HBM copy rate."""
+    import bench
+
+    class Mach:
+        sm_count = 152
+    pk = {"hbm_gbs": 6800.0, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1700.0,
+          "sm_max_mhz": 2000.0}
+    clocks = {"sm_mhz": 1000.0}
+    r = bench.roofline("f32", {"flops": 2e12}, [40.0], 40.0, Mach, pk, "t", clocks)
+    assert r["bound"] == "alu" and r["peak"] == pytest.approx(152 * 128 * 2 * 2000e6 / 1e12)
+    assert r["achieved"] == pytest.approx(50.0)
+    assert r["frac_at_observed_clock"] == pytest.approx(2 * r["frac"])
+    r = bench.roofline("split", {"flops": 6e12}, [3.0], 3.5, Mach, pk, "t", clocks, timed_s=0.1)
+    assert r["bound"] == "tensor" and r["peak"] == 2000.0 and r["achieved"] == pytest.approx(2000.0)
+    r = bench.roofline("split", {"flops": 6e12}, [3.0], 3.5, Mach, pk, "t", clocks, timed_s=2.0)
+    assert r["peak"] == 1700.0
+    r = bench.roofline("fp8", {"flops": 2e12}, [1.0], 1.2, Mach, pk, "t", clocks, timed_s=0.1)
+    assert r["peak"] == 4000.0
+    r = bench.roofline("split", {"flops": 1e11, "bytes": 6.8e9}, [2.0], 2.0, Mach, pk, "t", clocks)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["frac"] == pytest.approx(0.5)
+
+
+def test_reference_arm_prints_one_line():
+    """`bench.py --impl reference` runs the oracle on the host (no GPU needed) and
+    prints the contract's JSON line with the reference keys."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--size", "64", "--steps", "2", "--warmup", "3"],
+                         capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 2
+    for key in ("metric", "unit", "n_gpus", "ms_per_step", "higher_is_better", "cpu_baseline", "e2e"):
+        assert key in line
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
