@@ -177,7 +177,8 @@ def grouped(dev, stream):
     replay = lambda: g.replay()
     replay()
     t_sep_graph = _events_ms(replay, 10, stream)
-    # the tensor-core forms of the same group (three launches: A, B conversions, GEMM)
+    # the tensor-core forms of the same group (BF16 and split: one conversion launch for
+    # A and B, one GEMM launch; FP8: two quantisation launches and the GEMM)
     host_rows = []
     for i, (M, N, K) in enumerate(dims[:64]):
         A, B = inputs.gemm_operands(int(M), int(N), int(K), seed=1 + 2 * i, dist="normal")

@@ -102,14 +102,18 @@ typedef struct {
  *    B1 in {128, 256}) or B0 = 256 (BF16 and split only: B1 = 256, a cluster of
  *    two CTAs on the two SMs of a TPC per tile, each staging its 128 rows of A
  *    and half of the B^T rows, one tcgen05.mma with cta_group::2 and M = 256 for
- *    both); s = number of pipeline stages, sr unused (0), tile = K depth per
- *    stage (0 = natural: 64 for BF16/split, 128 for FP8).
- *    (128, 64, s): the fused-conversion program of the BF16 (s = 4) and split
+ *    both); s = number of pipeline stages, sr unused (0) but in the programs
+ *    below, tile = K depth per stage (0 = natural: 64 for BF16/split, 128 for FP8).
+ *    (128, 64, s, sr): the fused-conversion program of the BF16 (s = 4) and split
  *    (s = 3) forms for skinny products, N <= 64 (INFEASIBLE beyond): the GEMM
  *    reads A in FP32 by TMA and converts it to BF16 (hi and lo) in shared
  *    memory, so A crosses memory once; A must be 16-byte aligned with lda a
- *    multiple of 4 (else ALIGNMENT).  pgk_gemm without parameters takes it for
- *    N <= 64 when A qualifies. */
+ *    multiple of 4 (else ALIGNMENT).  sr >= 2 splits K into sr slices (work
+ *    units: 128-row tile x slice) whose partial products a second launch sums
+ *    in slice order (deterministic; a library workspace holds sr x M x N
+ *    floats); sr = 0 or 1: one slice.  pgk_gemm without parameters takes it
+ *    for N <= 64 when A qualifies, with as many slices as fill the SMs when the
+ *    row tiles alone do not (each slice at least 512 deep). */
 typedef struct { int B0, B1, s, sr, tile; } pgk_params;
 
 /* Leaves of the case discussion, with the paper's labels (Section 5):

@@ -380,6 +380,11 @@ struct TcParams {
     const int4* gtiles;
     const TcProb* gprobs;
     int ntiles_g;
+    // fused-conversion programs split over K: work unit t is K slice t % kslices of tile
+    // t / kslices (kper K blocks each, the last one shorter); slice s writes its partial
+    // product to part + s M N (row stride N), summed into C by a second launch
+    int kslices, kper;
+    float* part;
 };
 
 // Tensor maps of one launch: A and B^T (hi, and lo for the split forms), and B^T
@@ -423,7 +428,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
     const int nfull = tiles_m * tiles_n;
     const int tail = TAIL ? p.tail : 0;
     // work units: every tile, the last `tail` of them twice (one per column half)
-    const int ntiles = GROUPED ? p.ntiles_g : nfull + tail;
+    const int ksl = (Cfg::FUSED && p.kslices > 1) ? p.kslices : 1;
+    const int ntiles = GROUPED ? p.ntiles_g : (nfull + tail) * ksl;
     const int nkb = (p.K + Cfg::BK - 1) / Cfg::BK;
 
     if (threadIdx.x == 0) {
@@ -493,6 +499,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
     struct TileInfo {
         int tm, tn, M, N, nkb, rowA, rowB, ldc;
         int half;   // -1: the whole tile; 0 or 1: its first or second BN/2 columns
+        int kb0;    // first K block (a K slice of a fused-conversion program), else 0
+        int beta;
         float* C;
     };
     auto tile_info = [&](int t) {
@@ -510,9 +518,16 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             ti.ldc = q->ldc;
             ti.C = q->C;
             ti.half = -1;
+            ti.kb0 = 0;
+            ti.beta = p.beta;
         } else {
             int tt = t;
             ti.half = -1;
+            int sl = 0;
+            if (Cfg::FUSED && ksl > 1) {
+                sl = t % ksl;
+                tt = t / ksl;
+            }
             if (TAIL && t >= nfull - tail) {
                 const int j = t - (nfull - tail);
                 tt = nfull - tail + (j >> 1);
@@ -526,6 +541,15 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
             ti.rowB = 0;
             ti.ldc = p.ldc;
             ti.C = p.C;
+            ti.kb0 = 0;
+            ti.beta = p.beta;
+            if (Cfg::FUSED && ksl > 1) {
+                ti.kb0 = sl * p.kper;
+                ti.nkb = min(nkb - ti.kb0, p.kper);
+                ti.C = p.part + (size_t)sl * p.M * p.N;
+                ti.ldc = p.N;
+                ti.beta = 0;
+            }
         }
         return ti;
     };
@@ -545,7 +569,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 const int ya = ti.tm * Cfg::TM;
                 const int yb = ti.tn * Cfg::BN;
                 for (int kb = 0; kb < ti.nkb && ok; ++kb) {
-                    const int x = kb * Cfg::BK;
+                    const int x = (ti.kb0 + kb) * Cfg::BK;
                     if (!mbar_wait<Cfg::POLL>(&fempty_bar[fs], fphase ^ 1u, abort_flag, p.err,
                                               ERR_TIMEOUT_PRODUCER)) {
                         ok = false;
@@ -908,7 +932,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                                              (size_t)Cfg::FSTAGES * Cfg::F_BYTES) +
                     e * (32 * 33);
         auto store_block = [&](const float (&v)[32], int row0, int cb, int M, int N, float* C,
-                               int ldc) {
+                               int ldc, int beta) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) xp[lane * 33 + j] = v[j];
             __syncwarp();
@@ -919,7 +943,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                 if (row < M && col < N) {
                     float* cp = C + (size_t)row * ldc + col;
                     const float x = xp[rr * 33 + lane];
-                    *cp = p.beta ? *cp + x : x;
+                    *cp = beta ? *cp + x : x;
                 }
             }
             __syncwarp();
@@ -1066,7 +1090,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                         v[2 * i] = f2_lo(acc2[g * 16 + i]);
                         v[2 * i + 1] = f2_hi(acc2[g * 16 + i]);
                     }
-                    store_block(v, row0, n0 + g * 32, ti.M, tN, ti.C, ti.ldc);
+                    store_block(v, row0, n0 + g * 32, ti.M, tN, ti.C, ti.ldc, ti.beta);
                 }
             } else {
                 int w = 1;
@@ -1090,7 +1114,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, 1)
                     float v[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-                    store_block(v, row0, n0 + c * 32, ti.M, tN, ti.C, ti.ldc);
+                    store_block(v, row0, n0 + c * 32, ti.M, tN, ti.C, ti.ldc, ti.beta);
                 };
                 if (ti.half < 0) {
 #pragma unroll 1
@@ -1137,6 +1161,21 @@ __global__ void k_wait_selftest(unsigned int* err, unsigned long long limit_ns) 
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         mbar_wait(&bar, 0, &abort_sh, err, ERR_TIMEOUT_SELFTEST, limit_ns);
+    }
+}
+
+// Sum of the K-slice partials of a split fused-conversion launch, in slice order
+// (deterministic): C = sum_s part[s] (beta = 0) or C += sum_s part[s] (beta = 1).
+__global__ void k_slice_reduce(int M, int N, const float* __restrict__ part, int slices, float* C,
+                               int ldc, int beta) {
+    const long long total = (long long)M * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / N), c = (int)(i - (long long)r * N);
+        float acc = part[i];
+        for (int y = 1; y < slices; ++y) acc += part[(size_t)y * total + i];
+        float* cp = C + (size_t)r * ldc + c;
+        *cp = beta ? *cp + acc : acc;
     }
 }
 
@@ -1375,7 +1414,12 @@ pgk_status tc_select(const pgk_machine* m, int M, int N, int K, pgk_dtype dtype,
         c.threads = t[i].threads;
         c.params = *prog;
         c.params.tile = natural;
-        c.params.sr = 0;
+        // sr: the K slices of a fused-conversion program (0 or 1: one slice)
+        if (!t[i].fused) c.params.sr = 0;
+        else if (c.params.sr < 0 || c.params.sr > 1024) {
+            set_error("fused-conversion program: K slices (sr = %d) must lie in [0, 1024]", c.params.sr);
+            return PGK_ERR_INVALID_ARG;
+        }
         *out = c;
         return PGK_OK;
     }
@@ -1656,9 +1700,9 @@ pgk_status launch_quant_fp8(int rows, int cols, const float* src, int lds, uint8
 
 // The fused-conversion programs: B^T is prepared (BF16, or hi and lo) into a
 // library workspace, A is read in FP32 by the kernel itself.
-static pgk_status tc_gemm_fused(const TcVariant& v, int M, int N, int K, pgk_dtype dtype,
-                                const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                                int beta, cudaStream_t s, bool prep_b) {
+static pgk_status tc_gemm_fused(const TcVariant& v, int slices, int M, int N, int K,
+                                pgk_dtype dtype, const float* A, int lda, const float* B, int ldb,
+                                float* C, int ldc, int beta, cudaStream_t s, bool prep_b) {
     pgk_status st = get_encoder();
     if (st != PGK_OK) return st;
     if (((uintptr_t)A & 15u) != 0 || lda % 4 != 0) {
@@ -1700,9 +1744,26 @@ static pgk_status tc_gemm_fused(const TcVariant& v, int M, int N, int K, pgk_dty
     p.beta = beta ? 1 : 0;
     p.err = device_error_word(&st);
     if (!p.err) return st;
-    const long long tiles = (long long)((M + v.BM - 1) / v.BM) * ((N + v.BN - 1) / v.BN);
+    // K slices: every slice gets at least one K block
+    const int nkb = (K + 63) / 64;
+    int S = std::max(1, std::min(slices, nkb));
+    const int kper = (nkb + S - 1) / S;
+    S = (nkb + kper - 1) / kper;
+    p.kslices = S;
+    p.kper = kper;
+    if (S > 1) {
+        p.part = (float*)workspace(WS_SPLITK, sizeof(float) * (size_t)S * M * N, &st);
+        if (!p.part) return st;
+    }
+    const long long tiles = (long long)((M + v.BM - 1) / v.BM) * ((N + v.BN - 1) / v.BN) * S;
     cudaError_t e = v.launch(maps, p, tiles, m.sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "fused-conversion GEMM launch");
+    if (S > 1) {
+        const long long total = (long long)M * N;
+        const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)m.sm_count * 8);
+        k_slice_reduce<<<blocks, 256, 0, s>>>(M, N, p.part, S, C, ldc, p.beta);
+        PGK_CUDA_TRY(cudaGetLastError(), "K-slice reduction launch");
+    }
     return PGK_OK;
 }
 
@@ -1716,7 +1777,8 @@ pgk_status tc_gemm_fp32_inputs(const pgk_case& c, int M, int N, int K, pgk_dtype
         const TcVariant* t = tc_table(&n);
         const int i = c.variant_id - tc_base_id;
         if (i >= 0 && i < n && t[i].fused)
-            return tc_gemm_fused(t[i], M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, s, prep_b);
+            return tc_gemm_fused(t[i], c.params.sr, M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, s,
+                                 prep_b);
     }
     const int Kp = (K + 15) / 16 * 16;
     const int esz = dtype == PGK_FP8_E4M3 ? 1 : 2;

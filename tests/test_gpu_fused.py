@@ -125,3 +125,54 @@ def test_fused_program_conditions(dev):
     assert oracle.rel_frobenius(Cd.cpu().numpy(), ref) <= 2e-5
 
 
+
+
+@pytest.mark.parametrize("form,fused,twopass", FORMS)
+@pytest.mark.parametrize("M,N,K,slices", [(300, 64, 1000, 2), (129, 17, 4099, 5), (1024, 64, 8192, 19),
+                                          (200, 40, 130, 7)])
+def test_k_slices(dev, form, fused, twopass, M, N, K, slices):
+    """K split over slices (sr >= 2; the last slice shorter where the K blocks do
+    not divide; more slices than K blocks give one block each): against the FP64
+    oracle within the form's tolerance, against the one-slice program within the
+    FP32 accumulation bound, and beta = 1 adds C once."""
+    A, B = inputs.gemm_operands(M, N, K, seed=5 * M + N + K, dist="normal")
+    lda = (K + 3) // 4 * 4
+    Aw = torch.zeros((M, lda), device=dev)
+    Aw[:, :K] = torch.from_numpy(A)
+    At, Bt = Aw[:, :K], torch.from_numpy(B).to(dev)
+    C1 = torch.empty(M, N, device=dev)
+    pgk.gemm(At, Bt, C1, form, pgk.params(*fused, 0, 0))
+    C0 = torch.randn(M, N, device=dev)
+    Cs = C0.clone()
+    pgk.gemm(At, Bt, Cs, form, pgk.params(*fused, slices, 0), beta=1)
+    torch.cuda.synchronize()
+    pgk.check_device_error()
+    got = (Cs - C0).cpu().numpy().astype(np.float64)
+    one = C1.cpu().numpy().astype(np.float64)
+    ref = oracle.gemm(A, B)
+    absab = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64)
+    assert oracle.rel_frobenius(got, ref) <= TOL[form]
+    # one rounding per product term and per slice partial, plus the beta term
+    bound = (3 * K + slices + 4) * 2.0 ** -24 * (absab + np.abs(one)) * 2.0 + 1e-6
+    assert np.all(np.abs(got - one) <= bound + TOL[form] * np.abs(one))
+    if form == pgk.SPLIT_BF16:
+        assert np.all(np.abs(got - one) <= bound)
+
+
+@pytest.mark.parametrize("form,fused,twopass", FORMS)
+def test_few_row_tiles_take_k_slices(dev, form, fused, twopass):
+    """4096 x 16 x 65536 (32 row tiles): without parameters the fused program
+    splits K over slices to fill the SMs; the result meets the form's tolerance,
+    row by row."""
+    M, N, K = 4096, 16, 65536
+    A, B = inputs.gemm_operands(M, N, K, seed=1)
+    At, Bt = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    C = torch.empty(M, N, device=dev)
+    pgk.gemm(At, Bt, C, form, None)
+    torch.cuda.synchronize()
+    pgk.check_device_error()
+    rows = np.linspace(0, M - 1, 16).astype(np.int64)
+    ref = oracle.gemm(A, B, rows=rows)
+    got = C[torch.from_numpy(rows).to(dev)].cpu().numpy().astype(np.float64)
+    per_row = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert per_row.max() <= TOL[form]
