@@ -176,3 +176,24 @@ def test_few_row_tiles_take_k_slices(dev, form, fused, twopass):
     got = C[torch.from_numpy(rows).to(dev)].cpu().numpy().astype(np.float64)
     per_row = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert per_row.max() <= TOL[form]
+
+
+@pytest.mark.parametrize("form,fused,twopass", FORMS)
+def test_every_tiny_shape(dev, form, fused, twopass):
+    """Every M, N, K in [1, 9]: the fused program (one slice, and two slices where
+    K allows only one block, so the slice count falls back to one) equals the
+    two-pass program bit for bit, beta 0."""
+    import itertools
+    for M, N, K in itertools.product(range(1, 10), repeat=3):
+        A, B = inputs.gemm_operands(M, N, K, seed=M * 100 + N * 10 + K, dist="normal")
+        Aw = torch.zeros((M, 12), device=dev)
+        Aw[:, :K] = torch.from_numpy(A)
+        At, Bt = Aw[:, :K], torch.from_numpy(B).to(dev)
+        C0 = torch.full((M, N), float("nan"), device=dev)
+        ref = _two_pass(dev, form, twopass, At, Bt, C0, 0)
+        for slices in (0, 2):
+            C = C0.clone()
+            pgk.gemm(At, Bt, C, form, pgk.params(*fused, slices, 0))
+            assert torch.equal(C, ref), (form, M, N, K, slices)
+    torch.cuda.synchronize()
+    pgk.check_device_error()
