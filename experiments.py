@@ -228,8 +228,9 @@ def _forms_at(M, N, K, dist, dev, stream):
         step_ms = _events_ms(run, 10, stream)
         err = _rel_err_rows(C, A, B, rows)
         kern_ms = step_ms
-        pipe = 2.0
-        if dt != pgk.F32:
+        pipe = 6.0 if dt == pgk.SPLIT_BF16 else 2.0
+        # a fused-conversion program (B1 = 64) reads FP32 A itself: its call is the kernel
+        if dt != pgk.F32 and best.B1 != 64:
             Kp = (K + 15) // 16 * 16
             if dt == pgk.FP8_E4M3:
                 a = torch.empty(M, Kp, dtype=torch.uint8, device=dev)
@@ -247,7 +248,6 @@ def _forms_at(M, N, K, dist, dev, stream):
                 pgk.cvt_bf16(Bd, b, 1, stream=sh)
                 k = lambda: pgk.gemm_lowp(M, N, K, dt, a, Kp, b, Kp, C, N, prog=best, stream=sh)
             else:
-                pipe = 6.0
                 a = torch.empty(M, Kp, dtype=torch.int16, device=dev)
                 al = torch.empty_like(a)
                 b = torch.empty(N, Kp, dtype=torch.int16, device=dev)
