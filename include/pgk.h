@@ -111,9 +111,9 @@ typedef struct {
  *    multiple of 4 (else ALIGNMENT).  sr >= 2 splits K into sr slices (work
  *    units: 128-row tile x slice) whose partial products a second launch sums
  *    in slice order (deterministic; a library workspace holds sr x M x N
- *    floats); sr = 0 or 1: one slice.  pgk_gemm without parameters takes it
- *    for N <= 64 when A qualifies, with as many slices as fill the SMs when the
- *    row tiles alone do not (each slice at least 512 deep). */
+ *    floats); sr = 1: one slice; sr = 0: as many slices as fill the SMs when
+ *    the row tiles alone do not, each at least 512 deep.  pgk_gemm without
+ *    parameters takes (128, 64, s, 0) for N <= 64 when A qualifies. */
 typedef struct { int B0, B1, s, sr, tile; } pgk_params;
 
 /* Leaves of the case discussion, with the paper's labels (Section 5):

@@ -438,11 +438,8 @@ pgk_status gemm_device(int M, int N, int K, pgk_dtype dtype, const float* A, int
         const bool fused = (dtype == PGK_BF16 || dtype == PGK_SPLIT_BF16) && N <= 64 &&
                            ((uintptr_t)A & 15u) == 0 && lda % 4 == 0;
         if (fused) {
-            // K slices when the 128-row tiles leave SMs idle: as many as fill the SMs,
-            // each at least 8 K blocks deep
-            const int tiles_m = (M + 127) / 128;
-            const int slices = tiles_m < m.sm_count ? std::min(m.sm_count / tiles_m, (K + 511) / 512) : 1;
-            p = pgk_params{128, 64, dtype == PGK_SPLIT_BF16 ? 3 : 4, slices > 1 ? slices : 0, 0};
+            // sr = 0: the program chooses its K slices for the shape
+            p = pgk_params{128, 64, dtype == PGK_SPLIT_BF16 ? 3 : 4, 0, 0};
         } else if (learned_select(M, N, K, dtype, A, lda, B, ldb, C, ldc, beta, stream, &p) !=
                    PGK_OK) {
             p = default_params(M, N, K, dtype);

@@ -1414,7 +1414,7 @@ pgk_status tc_select(const pgk_machine* m, int M, int N, int K, pgk_dtype dtype,
         c.threads = t[i].threads;
         c.params = *prog;
         c.params.tile = natural;
-        // sr: the K slices of a fused-conversion program (0 or 1: one slice)
+        // sr: the K slices of a fused-conversion program (0: chosen for the shape)
         if (!t[i].fused) c.params.sr = 0;
         else if (c.params.sr < 0 || c.params.sr > 1024) {
             set_error("fused-conversion program: K slices (sr = %d) must lie in [0, 1024]", c.params.sr);
@@ -1744,8 +1744,13 @@ static pgk_status tc_gemm_fused(const TcVariant& v, int slices, int M, int N, in
     p.beta = beta ? 1 : 0;
     p.err = device_error_word(&st);
     if (!p.err) return st;
-    // K slices: every slice gets at least one K block
+    // K slices: slices = 0 takes as many as fill the SMs when the 128-row tiles alone
+    // do not, each at least 8 K blocks (512) deep; every slice gets at least one K block
     const int nkb = (K + 63) / 64;
+    if (slices == 0) {
+        const int tiles_m = (M + v.BM - 1) / v.BM;
+        slices = tiles_m < m.sm_count ? std::min(m.sm_count / tiles_m, (K + 511) / 512) : 1;
+    }
     int S = std::max(1, std::min(slices, nkb));
     const int kper = (nkb + S - 1) / S;
     S = (nkb + kper - 1) / kper;

@@ -127,7 +127,7 @@ def test_tensor_core_case_selection(built):
             st, _ = pgk.select_case(m, 8192, 8192, 8192, form, pgk.params(*bad, 0, 0),
                                     raise_on_error=False)
             assert st == 3, (form, bad)
-    # K slices of the fused-conversion program: kept in the case, bounded
+    # K slices of the fused-conversion program (0: chosen at launch): kept in the case, bounded
     st, c = pgk.select_case(m, 4096, 16, 65536, pgk.SPLIT_BF16, pgk.params(128, 64, 3, 4, 0),
                             raise_on_error=False)
     assert st == 0 and c.params.sr == 4

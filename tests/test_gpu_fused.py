@@ -54,9 +54,10 @@ def _two_pass(dev, form, prog, A, B, C0, beta):
 @pytest.mark.parametrize("M,N,K", [(300, 64, 1000), (129, 17, 200), (1, 1, 1), (256, 64, 64),
                                    (513, 40, 130), (1000, 64, 4099), (2000, 33, 3000)])
 def test_fused_equals_two_pass(dev, form, fused, twopass, M, N, K):
-    """Ragged M (tiles of 128 rows), N (one 64-wide tile), K (64-deep blocks,
-    FP32 boxes of 32 columns past the end read as zeros), beta 0 and 1.  A is a
-    view with its row stride rounded up to 4 elements (16 bytes), as TMA needs."""
+    """One K slice (sr = 1); ragged M (tiles of 128 rows), N (one 64-wide tile), K
+    (64-deep blocks, FP32 boxes of 32 columns past the end read as zeros), beta 0
+    and 1.  A is a view with its row stride rounded up to 4 elements (16 bytes),
+    as TMA needs."""
     A, B = inputs.gemm_operands(M, N, K, seed=M + 3 * N + 7 * K, dist="normal")
     lda = (K + 3) // 4 * 4
     Aw = torch.full((M, lda), float("nan"), device=dev)
@@ -66,7 +67,7 @@ def test_fused_equals_two_pass(dev, form, fused, twopass, M, N, K):
         C0 = torch.randn(M, N, device=dev) if beta else torch.full((M, N), float("nan"), device=dev)
         ref = _two_pass(dev, form, twopass, At, Bt, C0, beta)
         C = C0.clone()
-        pgk.gemm(At, Bt, C, form, pgk.params(*fused, 0, 0), beta=beta)
+        pgk.gemm(At, Bt, C, form, pgk.params(*fused, 1, 0), beta=beta)
         torch.cuda.synchronize()
         pgk.check_device_error()
         assert not torch.isnan(C).any()
@@ -141,7 +142,7 @@ def test_k_slices(dev, form, fused, twopass, M, N, K, slices):
     Aw[:, :K] = torch.from_numpy(A)
     At, Bt = Aw[:, :K], torch.from_numpy(B).to(dev)
     C1 = torch.empty(M, N, device=dev)
-    pgk.gemm(At, Bt, C1, form, pgk.params(*fused, 0, 0))
+    pgk.gemm(At, Bt, C1, form, pgk.params(*fused, 1, 0))
     C0 = torch.randn(M, N, device=dev)
     Cs = C0.clone()
     pgk.gemm(At, Bt, Cs, form, pgk.params(*fused, slices, 0), beta=1)
@@ -180,9 +181,9 @@ def test_few_row_tiles_take_k_slices(dev, form, fused, twopass):
 
 @pytest.mark.parametrize("form,fused,twopass", FORMS)
 def test_every_tiny_shape(dev, form, fused, twopass):
-    """Every M, N, K in [1, 9]: the fused program (one slice, and two slices where
-    K allows only one block, so the slice count falls back to one) equals the
-    two-pass program bit for bit, beta 0."""
+    """Every M, N, K in [1, 9]: the fused program (one slice, two slices where K
+    allows only one block so the count falls back to one, and the automatic count)
+    equals the two-pass program bit for bit, beta 0."""
     import itertools
     for M, N, K in itertools.product(range(1, 10), repeat=3):
         A, B = inputs.gemm_operands(M, N, K, seed=M * 100 + N * 10 + K, dist="normal")
@@ -191,7 +192,7 @@ def test_every_tiny_shape(dev, form, fused, twopass):
         At, Bt = Aw[:, :K], torch.from_numpy(B).to(dev)
         C0 = torch.full((M, N), float("nan"), device=dev)
         ref = _two_pass(dev, form, twopass, At, Bt, C0, 0)
-        for slices in (0, 2):
+        for slices in (1, 2, 0):
             C = C0.clone()
             pgk.gemm(At, Bt, C, form, pgk.params(*fused, slices, 0))
             assert torch.equal(C, ref), (form, M, N, K, slices)

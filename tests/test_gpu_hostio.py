@@ -151,16 +151,16 @@ def test_tuned_program_runs_every_panel(dev):
 
 @pytest.mark.parametrize("dtype", [pgk.SPLIT_BF16, pgk.BF16])
 def test_skinny_host_buffers_take_the_fused_program(dev, dtype):
-    """N <= 64 on host buffers: with the fused-conversion program every row panel
-    reads its A in FP32 (B converted once) and the result equals the device path
-    with the same program bit for bit; without parameters each panel selects it
-    (with K slices where its row tiles leave SMs idle) and meets the form's
-    tolerance against the FP64 oracle."""
+    """N <= 64 on host buffers: with the fused-conversion program on one K slice
+    every row panel reads its A in FP32 (B converted once) and the result equals
+    the device path with the same program bit for bit; without parameters each
+    panel selects it (with K slices where its row tiles leave SMs idle) and meets
+    the form's tolerance against the FP64 oracle."""
     M, N, K = 1100, 64, 2048
     A, B = inputs.gemm_operands(M, N, K, seed=31)
     Ah, Bh = _host(A, True), _host(B, True)
     Ch = _host(np.full((M, N), np.nan, np.float32), True)
-    fused = pgk.params(128, 64, 3 if dtype == pgk.SPLIT_BF16 else 4, 0, 0)
+    fused = pgk.params(128, 64, 3 if dtype == pgk.SPLIT_BF16 else 4, 1, 0)   # one K slice
     pgk.gemm_host(Ah, Bh, Ch, dtype, fused)
     torch.cuda.synchronize()
     assert np.array_equal(Ch.numpy(), _device_result(dev, A, B, dtype, fused))
