@@ -15,6 +15,11 @@
 //   warps 2.. epilogue: tcgen05.ld the accumulator (one TMEM lane per output
 //           row), (FP8: scale each 128-deep chunk by sA*sB and add in
 //           registers), store FP32 C, release the accumulator.
+// The fused-conversion programs (128 x 64 tiles, N <= 64) add eight converter
+// warps after the epilogue warps: the producer loads A in FP32 into a ring of its
+// own and only B^T into the stages; the converters write A's BF16 tiles (hi, and
+// lo for split) into the stages.  Their work units may be K slices of a tile,
+// whose partial products k_slice_reduce sums in slice order.
 // Every wait is bounded (globaltimer); on timeout the CTA sets the device
 // error word, stops issuing, drains its own TMA and MMA work and frees TMEM.
 //
